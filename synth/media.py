@@ -1,0 +1,192 @@
+"""Seeded media and sources shaped like the paper's workloads.
+
+The paper's structures are random packed spheres made with an external tool
+(Sec. 4, first paragraph) that is not available here; the generators below draw
+comparable structures from ``numpy.random.default_rng(seed)``. They return the
+refractive index *without* absorbing layers (the solver adds those) and the
+source map S of the Helmholtz equation (Sec. 2, Eq. helmholtz).
+
+Nothing here computes any step of the modified Born series.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "spheres_medium",
+    "fill_spheres_medium",
+    "gaussian_random_field_medium",
+    "point_source",
+    "gaussian_beam_plane_source",
+    "random_field",
+    "CONFIGS",
+    "config_problem",
+]
+
+
+def _paint_sphere(n, centre, radius, value):
+    """Set every voxel whose centre lies within ``radius`` of ``centre``."""
+    lo = [max(0, int(np.floor(c - radius))) for c in centre]
+    hi = [min(s, int(np.ceil(c + radius)) + 1) for c, s in zip(centre, n.shape)]
+    if any(h <= l for l, h in zip(lo, hi)):
+        return 0
+    g = np.ogrid[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]]
+    d2 = (g[0] - centre[0]) ** 2 + (g[1] - centre[1]) ** 2 + (g[2] - centre[2]) ** 2
+    mask = d2 <= radius * radius
+    view = n[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]]
+    view[mask] = value
+    return int(mask.sum())
+
+
+def spheres_medium(shape, count, r_range, n_range, seed, background=1.0, margin=0,
+                   dtype=np.complex64):
+    """Background index plus ``count`` spheres painted in draw order.
+
+    Radii are uniform in ``r_range`` (pixels), centres uniform in the box shrunk
+    by ``margin`` pixels on every face, real indices uniform in ``n_range``.
+    Later spheres overwrite earlier ones where they overlap.
+    """
+    rng = np.random.default_rng(seed)
+    n = np.full(shape, background, dtype=dtype)
+    for _ in range(count):
+        r = rng.uniform(*r_range)
+        c = [rng.uniform(margin, max(margin, s - margin)) for s in shape]
+        v = rng.uniform(*n_range)
+        _paint_sphere(n, c, r, v)
+    return n
+
+
+def fill_spheres_medium(shape, fill, r_range, n_range, seed, background=1.0, margin=0,
+                        dtype=np.complex64, max_spheres=1_000_000):
+    """Add random spheres (overlap allowed) until at least ``fill`` of the voxels differ
+    from the background."""
+    rng = np.random.default_rng(seed)
+    n = np.full(shape, background, dtype=dtype)
+    total = int(np.prod(shape))
+    covered = np.zeros(shape, dtype=bool)
+    ncov = 0
+    for _ in range(max_spheres):
+        if ncov >= fill * total:
+            break
+        r = rng.uniform(*r_range)
+        c = [rng.uniform(margin, max(margin, s - margin)) for s in shape]
+        v = rng.uniform(*n_range)
+        lo = [max(0, int(np.floor(cc - r))) for cc in c]
+        hi = [min(s, int(np.ceil(cc + r)) + 1) for cc, s in zip(c, shape)]
+        if any(h <= l for l, h in zip(lo, hi)):
+            continue
+        g = np.ogrid[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]]
+        mask = (g[0] - c[0]) ** 2 + (g[1] - c[1]) ** 2 + (g[2] - c[2]) ** 2 <= r * r
+        sl = (slice(lo[0], hi[0]), slice(lo[1], hi[1]), slice(lo[2], hi[2]))
+        cv = covered[sl]
+        ncov += int((mask & ~cv).sum())
+        cv |= mask
+        n[sl][mask] = v
+    return n
+
+
+def gaussian_random_field_medium(shape, mean, std, corr_len, seed, dtype=np.complex64):
+    """``mean`` plus a Gaussian random field: white noise smoothed by the kernel
+    exp(-r^2/corr_len^2) (covariance proportional to exp(-r^2/(2 corr_len^2))),
+    rescaled to standard deviation ``std``. The smoothing is a periodic convolution
+    done with numpy's real FFT (input synthesis only)."""
+    rng = np.random.default_rng(seed)
+    noise = rng.standard_normal(shape)
+    spec = np.fft.rfftn(noise)
+    g = []
+    for s in shape:
+        d = np.minimum(np.arange(s), s - np.arange(s)).astype(np.float64)
+        g.append(np.exp(-(d ** 2) / corr_len ** 2))
+    kern = np.fft.rfftn(g[0][:, None, None] * g[1][None, :, None] * g[2][None, None, :])
+    field = np.fft.irfftn(spec * kern, s=shape)
+    field -= field.mean()
+    sd = field.std()
+    if sd > 0:
+        field *= std / sd
+    return (mean + field).astype(dtype)
+
+
+def point_source(shape, position=None, dtype=np.complex64):
+    """Unit source in one voxel (default: the voxel at index shape//2)."""
+    s = np.zeros(shape, dtype=dtype)
+    if position is None:
+        position = tuple(x // 2 for x in shape)
+    s[tuple(position)] = 1.0
+    return s
+
+
+def gaussian_beam_plane_source(shape, axis=2, index=16, waist=64.0, dtype=np.complex64):
+    """Flat-phase Gaussian profile exp(-rho^2/waist^2) on the plane ``axis == index``,
+    rho measured in pixels from the centre of that plane."""
+    s = np.zeros(shape, dtype=dtype)
+    others = [a for a in range(3) if a != axis]
+    c = [(shape[a] - 1) / 2.0 for a in others]
+    g0 = (np.arange(shape[others[0]]) - c[0]) ** 2
+    g1 = (np.arange(shape[others[1]]) - c[1]) ** 2
+    prof = np.exp(-(g0[:, None] + g1[None, :]) / waist ** 2)
+    idx = [slice(None)] * 3
+    idx[axis] = index
+    s[tuple(idx)] = prof
+    return s
+
+
+def random_field(shape, seed, dtype=np.complex64):
+    """Complex field with independent standard normal real and imaginary parts."""
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(dtype)
+
+
+# Workload table. Sizes, media and sources follow the configurations the paper's
+# experiments are shaped like (Sec. 4): 4 points per wavelength, random spheres,
+# absorbing layers, point or plane sources.
+CONFIGS = {
+    "C1": dict(shape=(64, 64, 64), pixel=0.25, wavelength=1.0, split=(1, 1, 1),
+               periodic=(True, True, True), widths=8, t=8, tol=1e-5,
+               medium=("spheres", dict(count=6, r_range=(3, 8), n_range=(1.2, 1.5), seed=101, margin=8)),
+               source=("point", dict())),
+    "C2": dict(shape=(256, 256, 256), pixel=0.25, wavelength=1.0, split=(2, 2, 2),
+               periodic=(False, False, False), widths=8, t=8, tol=1e-5,
+               medium=("spheres", dict(count=40, r_range=(4, 20), n_range=(1.0, 1.6), seed=102, margin=8)),
+               source=("point", dict())),
+    "C3": dict(shape=(512, 512, 512), pixel=0.25, wavelength=1.0, split=(4, 4, 4),
+               periodic=(False, False, False), widths=8, t=8, tol=1e-5,
+               medium=("grf", dict(mean=1.33, std=0.08, corr_len=6.0, seed=103)),
+               source=("beam", dict(axis=2, index=16, waist=64.0))),
+    "C5": dict(shape=(1280, 1280, 1280), pixel=0.25, wavelength=1.0, split=(4, 4, 4),
+               periodic=(False, False, False), widths=8, t=8, tol=1e-4,
+               medium=("fill", dict(fill=0.30, r_range=(5, 40), n_range=(1.0, 1.5), seed=105, margin=8)),
+               source=("point", dict())),
+}
+
+
+def config_problem(name, shape=None):
+    """Return ``(params, n, source)`` for a named workload.
+
+    ``shape`` overrides the grid (for reduced-size cases); the medium recipe is
+    kept. ``params`` holds the plan parameters as plain Python values.
+    """
+    cfg = dict(CONFIGS[name])
+    if shape is not None:
+        cfg["shape"] = tuple(shape)
+    shp = tuple(cfg["shape"])
+    kind, kw = cfg["medium"]
+    if kind == "spheres":
+        n = spheres_medium(shp, **kw)
+    elif kind == "fill":
+        n = fill_spheres_medium(shp, **kw)
+    elif kind == "grf":
+        n = gaussian_random_field_medium(shp, **kw)
+    else:
+        raise ValueError(kind)
+    skind, skw = cfg["source"]
+    if skind == "point":
+        src = point_source(shp, **skw)
+    elif skind == "beam":
+        src = gaussian_beam_plane_source(shp, **skw)
+    else:
+        raise ValueError(skind)
+    w = cfg["widths"]
+    params = dict(shape=shp, pixel=cfg["pixel"], wavelength=cfg["wavelength"],
+                  split=tuple(cfg["split"]), periodic=tuple(cfg["periodic"]),
+                  widths=((w, w), (w, w), (w, w)), t=cfg["t"], tol=cfg["tol"])
+    return params, n, src

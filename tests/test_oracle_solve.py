@@ -1,0 +1,90 @@
+"""Pins of the oracle's iteration (Eq. wavesim_iter) against exact solutions."""
+import numpy as np
+import pytest
+
+from oracle import Problem, relative_l2
+from tests import dense_reference as dr
+
+
+def test_converges_to_dense_lu_solution():
+    """MBS run to 1e-12 equals the direct solve of the truncated decomposed system."""
+    shape = (10, 8, 6)
+    rng = np.random.default_rng(11)
+    n = 1.0 + 0.4 * rng.random(shape)
+    p = Problem(n, 0.25, 1.0, widths=((2, 2), (2, 2), (1, 1)), split=(2, 2, 1),
+                periodic=(False, False, False), t=3)
+    S = np.zeros(shape, dtype=complex)
+    S[5, 3, 2] = 1.0
+    S[2, 6, 4] = 0.5j
+    A = dr.dense_A_truncated(p.shape, p.sizes, p.t, p.h, p.a, p.periodic, p.k2, p.c)
+    x_lu = np.linalg.solve(A, p.scaled_source(S).ravel()).reshape(shape)
+    x, iters, hist = p.solve(S, tol=1e-12, max_iter=20000)
+    assert iters < 20000
+    assert relative_l2(x, x_lu) < 1e-9
+
+
+def test_residual_starts_at_one_and_decreases_monotonically():
+    """eps_0 = 1 (x0 = 0) and the residual never rises (Sec. 2, Sec. 4.1)."""
+    shape = (16, 12, 8)
+    rng = np.random.default_rng(12)
+    n = 1.0 + 0.5 * rng.random(shape)
+    p = Problem(n, 0.25, 1.0, widths=((3, 3), (3, 3), (2, 2)), split=(2, 3, 1),
+                periodic=(False, False, False), t=4)
+    S = np.zeros(shape, dtype=complex)
+    S[8, 6, 4] = 1.0
+    _, _, hist = p.solve(S, tol=1e-8, max_iter=3000)
+    assert hist[0] == 1.0
+    h = np.array(hist)
+    assert np.all(h[1:] <= h[:-1] * (1 + 1e-12))
+
+
+def test_homogeneous_periodic_closed_form():
+    """Constant absorbing medium, periodic, one subdomain: psi = F^-1[S^/(|p|^2 - k^2)]."""
+    shape = (16, 12, 10)
+    h = 0.25
+    n = np.full(shape, 1.0 + 0.05j)
+    p = Problem(n, h, 1.0, periodic=(True, True, True))
+    S = np.zeros(shape, dtype=complex)
+    S[3, 4, 5] = 1.0
+    x, iters, _ = p.solve(S, tol=1e-12, max_iter=5000)
+    k2 = (2 * np.pi * (1.0 + 0.05j)) ** 2
+    p2 = sum(np.meshgrid(*[(2 * np.pi * np.fft.fftfreq(s, d=h)) ** 2 for s in shape], indexing="ij"))
+    ref = np.fft.ifftn(np.fft.fftn(S) / (p2 - k2))
+    assert relative_l2(x, ref) < 1e-9
+
+
+def test_green_function_1d():
+    """Empty medium, wrap removal and wide absorbing layers: the field equals the outgoing
+    1-D Green's function h*i*exp(ik|x|)/(2k) away from the source and layers (Sec. 4)."""
+    N, w, h, lam = 4096, 384, 0.25, 1.0
+    n = np.ones((N, 1, 1))
+    p = Problem(n, h, lam, widths=((w, w), (0, 0), (0, 0)), split=(1, 1, 1),
+                periodic=(False, True, True), t=8, kappa=0.25)
+    S = np.zeros((N, 1, 1), dtype=complex)
+    src = N // 2
+    S[src, 0, 0] = 1.0
+    x, iters, _ = p.solve(S, tol=1e-9, max_iter=40000)
+    k = 2 * np.pi / lam
+    i = np.arange(N)
+    dist = np.abs(i - src) * h
+    G = h * 1j * np.exp(1j * k * dist) / (2 * k)
+    sel = (np.abs(i - src) >= 16) & (i >= w + 16) & (i < N - w - 16)
+    err = np.abs(x[:, 0, 0][sel] - G[sel]).max() / np.abs(G[sel]).max()
+    assert err < 1e-3
+
+
+def test_decomposition_matches_single_domain_solution():
+    """Different splits of one problem solve the same truncated system; the
+    difference to the undecomposed solve is the truncation error (Sec. 4.1)."""
+    shape = (32, 16, 1)
+    rng = np.random.default_rng(13)
+    n = 1.0 + 0.3 * rng.random(shape)
+    S = np.zeros(shape, dtype=complex)
+    S[16, 8, 0] = 1.0
+    kw = dict(widths=((4, 4), (4, 4), (0, 0)), periodic=(False, False, True), t=8)
+    x1, _, _ = Problem(n, 0.25, 1.0, split=(1, 1, 1), **kw).solve(S, tol=1e-11, max_iter=20000)
+    x2, it2, _ = Problem(n, 0.25, 1.0, split=(2, 1, 1), **kw).solve(S, tol=1e-11, max_iter=20000)
+    x4, it4, _ = Problem(n, 0.25, 1.0, split=(4, 2, 1), **kw).solve(S, tol=1e-11, max_iter=20000)
+    e2 = relative_l2(x2, x1) ** 2
+    e4 = relative_l2(x4, x1) ** 2
+    assert e2 < 1e-3 and e4 < 1e-3      # squared metric of Sec. 4.1
