@@ -1,0 +1,209 @@
+/*
+ * mbs.h - C ABI of the GB300 modified Born series (MBS) Helmholtz solver with
+ * block domain decomposition (Mache & Vellekoop, "Domain decomposition of the
+ * modified Born series approach for large-scale wave propagation simulations").
+ *
+ * Problem (Sec. 2, Eq. helmholtz and Eq. LV): (laplacian + k^2) psi = -S on a
+ * regular 3-D grid, k(r) = 2 pi n(r) / lambda, rescaled as A x = y with
+ * A = c (laplacian + k^2), x = psi, y = -c S. A is split as L + V where L is the
+ * angular-spectrum convolution c F^-1(k0^2 - |p|^2) F taken separately on every
+ * subdomain (Sec. 3, Eq. LV_block) and V holds the scattering potential
+ * c (k^2 - k0^2) plus the truncated t x t wrap-removal and transfer blocks of the
+ * subdomain edges (Sec. 3, Figs. 4-5; Sec. 3.1 steps 1-5). The solve is the
+ * preconditioned Richardson iteration of Eq. wavesim_iter with the scale c of
+ * Eq. c_scale2 and relaxation alpha (0.75, Eq. c_scale).
+ *
+ * Conventions
+ *  - Arrays are complex64 (interleaved float real, imaginary), C order, shape
+ *    (n0, n1, n2); axis 0 is the slowest (the paper's x axis).
+ *  - Pointers may be device pointers or host pointers; the library inspects
+ *    each pointer (cudaPointerGetAttributes) and copies host data through the
+ *    plan's stream. Host copies are counted in the timing of the call.
+ *  - Every call is synchronous with respect to the host unless stated, and all
+ *    device work runs on the plan's stream.
+ *  - Errors are returned as mbs_status; nothing is thrown or aborted across the
+ *    ABI. mbs_last_error() returns a thread-local description of the last error.
+ *  - Ownership: the caller owns every array passed in; the plan copies what it
+ *    needs and owns its device buffers (or the caller-provided workspace).
+ *  - There is no CPU fallback: without a CUDA device every compute call fails
+ *    with MBS_ECUDA.
+ */
+#ifndef MBS_GB300_H
+#define MBS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MBS_API __attribute__((visibility("default")))
+#else
+#define MBS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mbs_plan mbs_plan;
+
+typedef enum mbs_status {
+  MBS_OK = 0,
+  MBS_EINVAL = 1,      /* bad argument (shape, split, t, sizes, NaN in n, ...) */
+  MBS_ENOMEM = 2,      /* device memory insufficient (checked before allocating) */
+  MBS_ECUDA = 3,       /* CUDA runtime error or no device */
+  MBS_ENOCONV = 4,     /* max_iter reached before tol; out holds the last iterate */
+  MBS_ENAN = 5,        /* residual became NaN or Inf */
+  MBS_EDIVERGE = 6,    /* residual kept rising (the iteration is monotone in exact arithmetic, Sec. 2) */
+  MBS_ETIMEOUT = 7,    /* a bounded device wait expired */
+  MBS_EUNSUPPORTED = 8 /* size outside the compiled FFT lengths or limits below */
+} mbs_status;
+
+/* Operators for mbs_apply_operator (all act on the whole decomposed grid). */
+typedef enum mbs_operator {
+  MBS_OP_A = 0,         /* (L + V) x: the decomposed, truncated operator (Eq. LV_block)         */
+  MBS_OP_PRECOND = 1,   /* Gamma^-1 (y - A x), Gamma^-1 = (I - V)(L + I)^-1, y = -c S of the last
+                           mbs_set_source (zero if none) (Sec. 2, Eq. richardson)               */
+  MBS_OP_V = 2,         /* V x = c (k^2 - k0^2) x + E x (Sec. 3.1 steps 1-5)                     */
+  MBS_OP_L = 3,         /* L x = c F^-1 (k0^2 - |p|^2) F x per subdomain (Eq. L-convolution)     */
+  MBS_OP_PROPAGATE = 4, /* (L + I)^-1 x per subdomain                                            */
+  MBS_OP_E = 5,         /* E x: the edge-correction part of V alone                              */
+  MBS_OP_FFT = 6,       /* unnormalised forward DFT of every subdomain, in place of the subdomain */
+  MBS_OP_IFFT = 7       /* inverse DFT (1/n0 n1 n2) of every subdomain                           */
+} mbs_operator;
+
+/* Limits of this build. */
+#define MBS_MAX_SPLIT 16 /* subdomains per axis */
+#define MBS_MAX_T 32     /* truncation width */
+#define MBS_MAX_EDGE 512 /* longest subdomain edge; edges must factor into 2, 3, 5, 7 */
+
+/* Option flags. */
+#define MBS_FLAG_NO_GRAPH (1u << 0) /* launch kernels one by one instead of replaying a CUDA graph */
+
+typedef struct mbs_options {
+  int32_t truncation;        /* t, the kept edge width (Sec. 3, Fig. 5); 0 -> 8 (Sec. 3.3)      */
+  double alpha;              /* relaxation (Eq. c_scale); 0 -> 0.75                              */
+  uint32_t periodic_mask;    /* bit d set: axis d periodic. Periodic unsplit axis: no corrections
+                                (a_d = 0); periodic split axis: transfer across the seam (a_d = 2) */
+  double absorb_kappa;       /* peak imaginary index of the absorbing ramps; <0 -> 0.5           */
+  const int64_t *split_sizes;/* NULL (near-equal sizes, the first n mod S one larger) or
+                                split[0]+split[1]+split[2] explicit sizes, axis by axis           */
+  uint32_t flags;            /* MBS_FLAG_*                                                        */
+  int32_t graph_iters;       /* iterations per captured graph; 0 -> chosen by the plan            */
+  void *stream;              /* cudaStream_t for all work; NULL -> a non-blocking stream the plan creates */
+  void *workspace;           /* optional device workspace of workspace_bytes (see
+                                mbs_workspace_bytes); NULL -> the plan allocates its own          */
+  size_t workspace_bytes;
+} mbs_options;
+
+/* Fill *opts with the defaults above. */
+MBS_API void mbs_default_options(mbs_options *opts);
+
+/*
+ * Create a plan: the problem of Sec. 2 on a grid `shape` (n0, n1, n2) with pixel
+ * size `pixel_size` and vacuum wavelength `wavelength` (same length unit),
+ * refractive index `refractive_index` (complex64, shape; host or device), and
+ * absorbing layers of boundary_widths[2d], boundary_widths[2d+1] pixels on the
+ * low and high face of axis d (added inside the grid as a linear ramp of the
+ * imaginary index). `split` gives the subdomains per axis (Sec. 3: any number
+ * along any axis, unequal sizes allowed). The plan computes, in FP64 on the
+ * device: k^2, k0^2 (centre of the bounding box of k^2 in C), the scale c of
+ * Eq. c_scale2 with ||A12|| the spectral norm of the t x t block W, and the
+ * medium factor B = 1 - c (k^2 - k0^2) stored as complex64.
+ * Errors: MBS_EINVAL (shape < 1, split not in [1, MBS_MAX_SPLIT], t < 0 or
+ * > MBS_MAX_T, t larger than a subdomain edge on a corrected axis, non-finite n,
+ * wavelength or pixel size <= 0), MBS_EUNSUPPORTED (an edge not a compiled FFT
+ * length), MBS_ENOMEM (buffers do not fit; nothing is allocated), MBS_ECUDA.
+ */
+MBS_API mbs_status mbs_plan_create(mbs_plan **plan, const int64_t shape[3], double pixel_size, double wavelength,
+                           const void *refractive_index, const int32_t boundary_widths[6],
+                           const int32_t split[3], const mbs_options *opts);
+
+/* Device bytes a plan with these arguments needs (for a caller-provided workspace). */
+MBS_API mbs_status mbs_workspace_bytes(const int64_t shape[3], const int32_t split[3], const mbs_options *opts,
+                               size_t *bytes);
+
+typedef struct mbs_plan_info {
+  double c_re, c_im;         /* scale factor c (Eq. c_scale2)                                  */
+  double k0sq_re, k0sq_im;   /* background k0^2                                                */
+  double contrast;           /* ||k^2 - k0^2||_inf                                             */
+  double block_norm;         /* ||W||_2 in units of 1/h^2 (R2 reading of ||A12||)              */
+  int32_t a[3];              /* a_d of Eq. c_scale2                                            */
+  int32_t t;
+  double alpha;
+  int64_t shape[3];
+  int32_t split[3];
+  int64_t sizes[3][MBS_MAX_SPLIT];  /* subdomain edges along each axis                        */
+  size_t device_bytes;       /* device memory held by the plan                                 */
+  int32_t graph_iters;
+} mbs_plan_info;
+
+MBS_API mbs_status mbs_plan_get_info(const mbs_plan *plan, mbs_plan_info *info);
+
+/*
+ * out = op(x) for op in mbs_operator. x and out are complex64 arrays of the
+ * grid's shape (host or device); they must not alias. MBS_OP_FFT / MBS_OP_IFFT
+ * return every subdomain's transform in the subdomain's own box, k-space index
+ * in natural (FFT) order.
+ */
+MBS_API mbs_status mbs_apply_operator(mbs_plan *plan, int32_t which, const void *x, void *out);
+
+/*
+ * Start a solve: store the source S (complex64, shape; host or device; copied
+ * into the plan), set x = 0 and clear the residual history. The iteration uses
+ * y = -c S (Eq. LV); only the bounding box of S's non-zeros is read per step.
+ */
+MBS_API mbs_status mbs_set_source(mbs_plan *plan, const void *source);
+
+/*
+ * Run up to n_iter iterations of Eq. wavesim_iter from the current state,
+ * stopping after the update in which eps_n = ||r_n|| / ||r_0|| < tol (Sec. 3.1;
+ * r_n = Gamma^-1 (y - A x_n) is taken before update n, x_0 = 0, FP64 norms).
+ * *iters_done (nullable) receives the total iterations since mbs_set_source,
+ * *residual (nullable) the last eps. Returns MBS_OK if eps < tol was reached,
+ * MBS_ENOCONV if the budget ran out, MBS_ENAN / MBS_EDIVERGE on breakdown.
+ * If `no_poll` is non-zero the call enqueues all n_iter iterations without
+ * intermediate host synchronisation (for timing); it still synchronises once
+ * at the end.
+ */
+MBS_API mbs_status mbs_iterate(mbs_plan *plan, int32_t n_iter, double tol, int32_t no_poll, int32_t *iters_done,
+                       double *residual);
+
+/* Copy the current field x (complex64, shape) to out (host or device). */
+MBS_API mbs_status mbs_get_field(const mbs_plan *plan, void *out);
+
+/*
+ * Copy the residual history eps_0 .. eps_{n-1} (n = min(cap, iterations done))
+ * to host memory `history`; *n_out receives n.
+ */
+MBS_API mbs_status mbs_get_history(const mbs_plan *plan, double *history, int32_t cap, int32_t *n_out);
+
+/*
+ * Full solve: mbs_set_source(source), mbs_iterate(max_iter, tol), then the
+ * field to `out` (host or device; may alias `source`). `history` (nullable,
+ * host) receives up to max_iter residuals. Returns as mbs_iterate; on
+ * MBS_ENOCONV `out` holds the last iterate.
+ */
+MBS_API mbs_status mbs_solve(mbs_plan *plan, const void *source, void *out, double tol, int32_t max_iter,
+                     int32_t *iters_out, double *residual_out, double *history);
+
+/*
+ * Timing support: run n_iter iterations (tol 0) launching kernels one by one
+ * with CUDA events around every launch on the plan's stream, and report per
+ * kernel kind the number of launches and the summed device milliseconds.
+ * kind names: mbs_kernel_kind_name(i) for i < MBS_KERNEL_KINDS.
+ */
+#define MBS_KERNEL_KINDS 8
+MBS_API mbs_status mbs_profile_iterations(mbs_plan *plan, int32_t n_iter, int32_t launches[MBS_KERNEL_KINDS],
+                                  double ms[MBS_KERNEL_KINDS]);
+MBS_API const char *mbs_kernel_kind_name(int32_t kind);
+
+MBS_API void mbs_plan_destroy(mbs_plan *plan);
+
+/* Thread-local description of the last error (empty string if none). */
+MBS_API const char *mbs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBS_GB300_H */

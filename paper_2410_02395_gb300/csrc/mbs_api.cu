@@ -1,0 +1,1033 @@
+// Host side of the MBS library: plan creation, operator application, the
+// iteration driver (CUDA-graph replays with a device-side stop flag) and the
+// C ABI declared in include/mbs.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mbs.h"
+#include "mbs_internal.h"
+
+using namespace mbs;
+
+namespace {
+
+thread_local std::string g_err;
+
+mbs_status fail(mbs_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CU(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(MBS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+constexpr int kHistCap = 1 << 16;
+constexpr int kShellBlocks = 152 * 8;
+constexpr int kSetupBlocks = 152 * 4;
+
+struct SizeGroup {
+  int n;
+  int nsub;
+  int subs[kMaxSplit];
+};
+
+// Host FP64 kernel of the band-limited second derivative on the infinite grid
+// (Sec. 3, Fig. 4): D(0) = -pi^2/(3h^2), D(m) = -2(-1)^m/(m^2 h^2).
+double sinc_d2(int m, double h) {
+  if (m == 0) return -M_PI * M_PI / (3.0 * h * h);
+  const double s = (m % 2 != 0) ? -1.0 : 1.0;
+  return -2.0 * s / ((double)m * m * h * h);
+}
+
+// Largest singular value of a t x t matrix: cyclic Jacobi on W^T W.
+double spectral_norm(const std::vector<double>& W, int t) {
+  if (t == 0) return 0.0;
+  std::vector<double> A(t * t, 0.0);
+  for (int i = 0; i < t; i++)
+    for (int j = 0; j < t; j++) {
+      double s = 0.0;
+      for (int k = 0; k < t; k++) s += W[k * t + i] * W[k * t + j];
+      A[i * t + j] = s;
+    }
+  for (int sweep = 0; sweep < 100; sweep++) {
+    double off = 0.0;
+    for (int p = 0; p < t; p++)
+      for (int q = p + 1; q < t; q++) off += A[p * t + q] * A[p * t + q];
+    if (off < 1e-30) break;
+    for (int p = 0; p < t; p++)
+      for (int q = p + 1; q < t; q++) {
+        const double apq = A[p * t + q];
+        if (fabs(apq) < 1e-300) continue;
+        const double theta = (A[q * t + q] - A[p * t + p]) / (2.0 * apq);
+        const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(tt * tt + 1.0), s = tt * c;
+        for (int k = 0; k < t; k++) {
+          const double akp = A[k * t + p], akq = A[k * t + q];
+          A[k * t + p] = c * akp - s * akq;
+          A[k * t + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < t; k++) {
+          const double apk = A[p * t + k], aqk = A[q * t + k];
+          A[p * t + k] = c * apk - s * aqk;
+          A[q * t + k] = s * apk + c * aqk;
+        }
+      }
+  }
+  double mx = 0.0;
+  for (int i = 0; i < t; i++) mx = std::max(mx, A[i * t + i]);
+  return sqrt(std::max(mx, 0.0));
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct mbs_plan {
+  // problem
+  int64_t N[3];
+  int S[3];
+  std::vector<int> sizes[3], offs[3];
+  double h, lambda, alpha, kappa;
+  int t;
+  uint32_t periodic;
+  int widths[6];
+  int a[3];
+  double c_re, c_im, k0_re, k0_im, contrast, wnorm;
+  bool has_shell;
+  uint32_t flags;
+  int graph_iters;
+  // device
+  cudaStream_t stream;
+  bool own_stream;
+  void* base;
+  bool own_base;
+  size_t bytes;
+  float2 *x, *B, *K, *src;
+  float2* tmp_in;
+  float2* tmp_out;
+  float *p2[3], *invn[3];
+  int *sub[3], *loc[3], *sh2list;
+  unsigned char* shell[3];
+  int nsh2;
+  float2* cW;
+  std::map<int, float2*> tw;
+  double* partials;
+  int n_rows_partials, n_shell_partials;
+  DevState* state;
+  DevState* free_state;  // never marked done (operator applications)
+  double* history;
+  int* box_dev;
+  double* host_pinned;  // 64 doubles
+  DevState* host_state;
+  GridDesc g;
+  AxisTables tb;
+  std::vector<SizeGroup> groups[3];
+  int64_t sbox[6];
+  bool have_source;
+  // graph
+  cudaGraphExec_t graph;
+  bool graph_ready;
+};
+
+namespace {
+
+int64_t nvox(const mbs_plan* p) { return p->N[0] * p->N[1] * p->N[2]; }
+
+void build_groups(mbs_plan* p) {
+  for (int d = 0; d < 3; d++) {
+    p->groups[d].clear();
+    std::map<int, SizeGroup> m;
+    for (int s = 0; s < p->S[d]; s++) {
+      const int n = p->sizes[d][s];
+      auto it = m.find(n);
+      if (it == m.end()) {
+        SizeGroup gsz;
+        gsz.n = n;
+        gsz.nsub = 0;
+        it = m.emplace(n, gsz).first;
+      }
+      it->second.subs[it->second.nsub++] = s;
+    }
+    for (auto& kv : m) p->groups[d].push_back(kv.second);
+  }
+}
+
+size_t layout(mbs_plan* p, char* base, bool assign) {
+  size_t off = 0;
+  auto take = [&](size_t b) -> char* {
+    char* r = base ? base + off : nullptr;
+    off += align256(b);
+    return r;
+  };
+  const size_t F = (size_t)nvox(p) * sizeof(float2);
+  char* px = take(F);
+  char* pB = take(F);
+  char* pK = take(F);
+  char* psrc = take(F);
+  char *pp2[3], *pinv[3], *psub[3], *ploc[3], *psh[3];
+  for (int d = 0; d < 3; d++) {
+    pp2[d] = take(p->N[d] * sizeof(float));
+    pinv[d] = take(p->N[d] * sizeof(float));
+    psub[d] = take(p->N[d] * sizeof(int));
+    ploc[d] = take(p->N[d] * sizeof(int));
+    psh[d] = take(p->N[d]);
+  }
+  char* psh2 = take(p->N[2] * sizeof(int));
+  char* pcw = take(std::max(1, p->t * p->t) * sizeof(float2));
+  std::map<int, char*> ptw;
+  for (int d = 0; d < 3; d++)
+    for (auto& gsz : p->groups[d])
+      if (!ptw.count(gsz.n)) ptw[gsz.n] = take(gsz.n * sizeof(float2));
+  const int64_t rows = p->N[0] * p->N[1];
+  const int nrb = (int)((rows + 31) / 32);
+  const int nrows_partials = nrb * p->S[2];
+  const int npart = nrows_partials + kShellBlocks + 6 * kSetupBlocks;
+  char* ppart = take(npart * sizeof(double));
+  char* pst = take(sizeof(DevState));
+  char* pfst = take(sizeof(DevState));
+  char* phist = take(kHistCap * sizeof(double));
+  char* pbox = take(6 * sizeof(int));
+  if (assign) {
+    p->x = (float2*)px;
+    p->B = (float2*)pB;
+    p->K = (float2*)pK;
+    p->src = (float2*)psrc;
+    for (int d = 0; d < 3; d++) {
+      p->p2[d] = (float*)pp2[d];
+      p->invn[d] = (float*)pinv[d];
+      p->sub[d] = (int*)psub[d];
+      p->loc[d] = (int*)ploc[d];
+      p->shell[d] = (unsigned char*)psh[d];
+    }
+    p->sh2list = (int*)psh2;
+    p->cW = (float2*)pcw;
+    p->tw.clear();
+    for (auto& kv : ptw) p->tw[kv.first] = (float2*)kv.second;
+    p->partials = (double*)ppart;
+    p->n_rows_partials = nrows_partials;
+    p->n_shell_partials = kShellBlocks;
+    p->state = (DevState*)pst;
+    p->free_state = (DevState*)pfst;
+    p->history = (double*)phist;
+    p->box_dev = (int*)pbox;
+  }
+  return off;
+}
+
+mbs_status validate_and_fill(mbs_plan* p, const int64_t shape[3], double h, double lambda, const int32_t widths[6],
+                             const int32_t split[3], const mbs_options* o) {
+  if (!shape || !split) return fail(MBS_EINVAL, "shape and split are required");
+  if (!(h > 0.0) || !(lambda > 0.0) || !isfinite(h) || !isfinite(lambda))
+    return fail(MBS_EINVAL, "pixel size and wavelength must be positive and finite");
+  p->h = h;
+  p->lambda = lambda;
+  p->t = (o && o->truncation > 0) ? o->truncation : 8;
+  if (o && o->truncation < 0) return fail(MBS_EINVAL, "truncation must be >= 0");
+  if (p->t > kMaxT) return fail(MBS_EINVAL, "truncation exceeds MBS_MAX_T");
+  p->alpha = (o && o->alpha > 0.0) ? o->alpha : 0.75;
+  p->kappa = (o && o->absorb_kappa >= 0.0) ? o->absorb_kappa : 0.5;
+  p->periodic = o ? o->periodic_mask : 0u;
+  p->flags = o ? o->flags : 0u;
+  p->graph_iters = (o && o->graph_iters > 0) ? o->graph_iters : 0;
+  int k = 0;
+  for (int d = 0; d < 3; d++) {
+    if (shape[d] < 1 || shape[d] > (1 << 20)) return fail(MBS_EINVAL, "grid extents must be in [1, 2^20]");
+    if (split[d] < 1 || split[d] > kMaxSplit) return fail(MBS_EINVAL, "split must be in [1, MBS_MAX_SPLIT]");
+    if (split[d] > shape[d]) return fail(MBS_EINVAL, "more subdomains than voxels along an axis");
+    p->N[d] = shape[d];
+    p->S[d] = split[d];
+    p->sizes[d].assign(split[d], 0);
+    p->offs[d].assign(split[d], 0);
+    if (o && o->split_sizes) {
+      int64_t tot = 0;
+      for (int s = 0; s < split[d]; s++) {
+        const int64_t v = o->split_sizes[k++];
+        if (v < 1) return fail(MBS_EINVAL, "explicit subdomain sizes must be >= 1");
+        p->sizes[d][s] = (int)v;
+        tot += v;
+      }
+      if (tot != shape[d]) return fail(MBS_EINVAL, "explicit subdomain sizes do not tile the axis");
+    } else {
+      const int64_t b = shape[d] / split[d], r = shape[d] % split[d];
+      for (int s = 0; s < split[d]; s++) p->sizes[d][s] = (int)(b + (s < r ? 1 : 0));
+    }
+    int acc = 0;
+    for (int s = 0; s < split[d]; s++) {
+      p->offs[d][s] = acc;
+      acc += p->sizes[d][s];
+    }
+    const bool per = (p->periodic >> d) & 1u;
+    p->a[d] = (split[d] == 1 && per) ? 0 : (split[d] == 1 ? 1 : 2);
+    for (int s = 0; s < split[d]; s++) {
+      const int n = p->sizes[d][s];
+      if (n > kMaxFFT || !fft_size_compiled(n))
+        return fail(MBS_EUNSUPPORTED, "subdomain edge " + std::to_string(n) +
+                                          " is not a compiled FFT length (2^a 3^b 5^c 7^d list, <= 512)");
+      if (p->a[d] > 0 && p->t > n) return fail(MBS_EINVAL, "truncation t exceeds a subdomain edge");
+    }
+  }
+  for (int i = 0; i < 6; i++) {
+    p->widths[i] = widths ? widths[i] : 0;
+    if (p->widths[i] < 0) return fail(MBS_EINVAL, "boundary widths must be >= 0");
+  }
+  return MBS_OK;
+}
+
+void fill_grid_desc(mbs_plan* p) {
+  GridDesc& g = p->g;
+  g.N0 = p->N[0];
+  g.N1 = p->N[1];
+  g.N2 = p->N[2];
+  g.t = p->t;
+  for (int d = 0; d < 3; d++) {
+    AxisDesc& ax = g.ax[d];
+    memset(&ax, 0, sizeof(ax));
+    ax.N = (int)p->N[d];
+    ax.S = p->S[d];
+    ax.a = p->a[d];
+    const bool per = (p->periodic >> d) & 1u;
+    for (int s = 0; s < p->S[d]; s++) {
+      ax.off[s] = p->offs[d][s];
+      ax.n[s] = p->sizes[d][s];
+      if (p->S[d] == 1) {
+        ax.left[s] = ax.right[s] = -1;
+      } else {
+        ax.left[s] = s > 0 ? s - 1 : (per ? p->S[d] - 1 : -1);
+        ax.right[s] = s < p->S[d] - 1 ? s + 1 : (per ? 0 : -1);
+      }
+    }
+  }
+  p->has_shell = p->t > 0 && (p->a[0] > 0 || p->a[1] > 0 || p->a[2] > 0);
+}
+
+mbs_status upload_tables(mbs_plan* p) {
+  for (int d = 0; d < 3; d++) {
+    const int N = (int)p->N[d];
+    std::vector<float> p2(N), invn(N);
+    std::vector<int> sub(N), loc(N);
+    std::vector<unsigned char> sh(N);
+    for (int s = 0; s < p->S[d]; s++) {
+      const int n = p->sizes[d][s], o = p->offs[d][s];
+      for (int q = 0; q < n; q++) {
+        const int qq = (2 * q < n) ? q : q - n;
+        const double pp = 2.0 * M_PI * qq / (n * p->h);
+        p2[o + q] = (float)(pp * pp);
+        invn[o + q] = (float)(1.0 / n);
+        sub[o + q] = s;
+        loc[o + q] = q;
+        sh[o + q] = (p->t > 0 && p->a[d] > 0 && (q < p->t || q >= n - p->t)) ? 1 : 0;
+      }
+    }
+    CU(cudaMemcpyAsync(p->p2[d], p2.data(), N * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+    CU(cudaMemcpyAsync(p->invn[d], invn.data(), N * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+    CU(cudaMemcpyAsync(p->sub[d], sub.data(), N * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+    CU(cudaMemcpyAsync(p->loc[d], loc.data(), N * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+    CU(cudaMemcpyAsync(p->shell[d], sh.data(), N, cudaMemcpyHostToDevice, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    if (d == 2) {
+      std::vector<int> list;
+      for (int i = 0; i < N; i++)
+        if (sh[i]) list.push_back(i);
+      p->nsh2 = (int)list.size();
+      if (!list.empty())
+        CU(cudaMemcpyAsync(p->sh2list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+      CU(cudaStreamSynchronize(p->stream));
+    }
+  }
+  for (auto& kv : p->tw) {
+    const int n = kv.first;
+    std::vector<float2> w(n);
+    for (int k = 0; k < n; k++) {
+      const double ang = -2.0 * M_PI * (double)k / n;
+      w[k] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+    CU(cudaMemcpyAsync(kv.second, w.data(), n * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+  }
+  AxisTables& tb = p->tb;
+  for (int d = 0; d < 3; d++) {
+    tb.p2[d] = p->p2[d];
+    tb.invn[d] = p->invn[d];
+    tb.sub[d] = p->sub[d];
+    tb.loc[d] = p->loc[d];
+    tb.shell[d] = p->shell[d];
+  }
+  tb.sh2list = p->sh2list;
+  tb.nsh2 = p->nsh2;
+  return MBS_OK;
+}
+
+// Medium set-up (Sec. 2): absorbing ramp, k^2, k0^2, contrast, c (Eq. c_scale2), B.
+mbs_status setup_medium(mbs_plan* p, const float2* n_dev) {
+  double* part = p->partials;
+  CU(launch_k2_bounds(n_dev, p->g, p->widths, p->kappa, p->lambda, part, kSetupBlocks, p->stream));
+  std::vector<double> hb(6 * kSetupBlocks);
+  CU(cudaMemcpyAsync(hb.data(), part, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  double mnr = 1e300, mxr = -1e300, mni = 1e300, mxi = -1e300, mxa = 0.0, bad = 0.0;
+  for (int b = 0; b < kSetupBlocks; b++) {
+    mnr = std::min(mnr, hb[6 * b + 0]);
+    mxr = std::max(mxr, hb[6 * b + 1]);
+    mni = std::min(mni, hb[6 * b + 2]);
+    mxi = std::max(mxi, hb[6 * b + 3]);
+    mxa = std::max(mxa, hb[6 * b + 4]);
+    bad += hb[6 * b + 5];
+  }
+  if (bad > 0.0 || !(mnr <= mxr)) return fail(MBS_EINVAL, "refractive index contains non-finite values");
+  p->k0_re = 0.5 * (mnr + mxr);
+  p->k0_im = 0.5 * (mni + mxi);
+  CU(launch_contrast(n_dev, p->g, p->widths, p->kappa, p->lambda, p->k0_re, p->k0_im, part, kSetupBlocks, p->stream));
+  std::vector<double> hc(kSetupBlocks);
+  CU(cudaMemcpyAsync(hc.data(), part, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  double m = 0.0;
+  for (double v : hc) m = std::max(m, v);
+  p->contrast = m;
+  // W[a][b] = D(t + b - a), its spectral norm, and c.
+  std::vector<double> W(p->t * p->t);
+  for (int i = 0; i < p->t; i++)
+    for (int j = 0; j < p->t; j++) W[i * p->t + j] = sinc_d2(p->t + j - i, p->h);
+  p->wnorm = spectral_norm(W, p->t);
+  double denom = m + (p->a[0] + p->a[1] + p->a[2]) * p->wnorm;
+  if (denom == 0.0) denom = 0.05 * mxa;
+  if (!(denom > 0.0)) return fail(MBS_EINVAL, "degenerate problem: zero wavenumber everywhere");
+  p->c_re = 0.0;
+  p->c_im = -0.95 / denom;
+  std::vector<float2> cw(std::max(1, p->t * p->t));
+  for (int i = 0; i < p->t * p->t; i++) cw[i] = make_float2((float)(p->c_re * W[i]), (float)(p->c_im * W[i]));
+  CU(cudaMemcpyAsync(p->cW, cw.data(), cw.size() * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+  CU(launch_make_B(n_dev, p->B, p->g, p->widths, p->kappa, p->lambda, p->k0_re, p->k0_im, p->c_re, p->c_im,
+                   kSetupBlocks, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  return MBS_OK;
+}
+
+PassArgs base_args(mbs_plan* p) {
+  PassArgs a;
+  memset(&a, 0, sizeof(a));
+  a.K = p->K;
+  a.B = p->B;
+  a.c = make_float2((float)p->c_re, (float)p->c_im);
+  const double ck0r = p->c_re * p->k0_re - p->c_im * p->k0_im;
+  const double ck0i = p->c_re * p->k0_im + p->c_im * p->k0_re;
+  a.ck0 = make_float2((float)ck0r, (float)ck0i);
+  a.mc = make_float2((float)-p->c_re, (float)-p->c_im);
+  a.alpha = (float)p->alpha;
+  a.tb = p->tb;
+  a.g = p->g;
+  return a;
+}
+
+ShellArgs shell_args(mbs_plan* p) {
+  ShellArgs s;
+  memset(&s, 0, sizeof(s));
+  s.K = p->K;
+  s.X = p->x;
+  s.B = p->B;
+  s.cW = p->cW;
+  s.alpha = (float)p->alpha;
+  s.tb = p->tb;
+  s.g = p->g;
+  return s;
+}
+
+int nrow_blocks(const mbs_plan* p) { return (int)((p->N[0] * p->N[1] + 31) / 32); }
+
+// Kernel kinds for profiling.
+enum { KK_SHELL_CORR = 0, KK_ROWS_FIRST, KK_STRIDED_FWD, KK_MID, KK_STRIDED_INV, KK_ROWS_LAST, KK_SHELL_FINAL, KK_FINALIZE };
+
+struct Recorder {
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>* ev = nullptr;
+  cudaStream_t st;
+  int kind = -1;
+  void begin(int k) {
+    if (!ev) return;
+    kind = k;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    ev->push_back({k, {a, b}});
+    cudaEventRecord(a, st);
+  }
+  void end() {
+    if (!ev) return;
+    cudaEventRecord(ev->back().second.second, st);
+  }
+};
+
+// The forward half shared by the iteration and several operators:
+// rows_first (mode), strided axis-1 forward, mid (mode), strided axis-1 inverse.
+cudaError_t run_transform_chain(mbs_plan* p, PassArgs a, int first_mode, int mid_mode, Recorder* rec) {
+  cudaError_t e;
+  const int nrb = nrow_blocks(p);
+  a.mode = first_mode;
+  for (auto& gz : p->groups[2]) {
+    a.nsub = gz.nsub;
+    memcpy(a.subs, gz.subs, sizeof(a.subs));
+    a.tw = p->tw[gz.n];
+    if (rec) rec->begin(KK_ROWS_FIRST);
+    e = launch_rows_first(gz.n, a, nrb, p->stream);
+    if (rec) rec->end();
+    if (e) return e;
+  }
+  for (auto& gy : p->groups[1]) {
+    if (gy.n == 1) continue;
+    a.nsub = gy.nsub;
+    memcpy(a.subs, gy.subs, sizeof(a.subs));
+    a.tw = p->tw[gy.n];
+    if (rec) rec->begin(KK_STRIDED_FWD);
+    e = launch_strided(gy.n, 1, false, a, p->stream);
+    if (rec) rec->end();
+    if (e) return e;
+  }
+  a.mode = mid_mode;
+  for (auto& gx : p->groups[0]) {
+    a.nsub = gx.nsub;
+    memcpy(a.subs, gx.subs, sizeof(a.subs));
+    a.tw = p->tw[gx.n];
+    if (rec) rec->begin(KK_MID);
+    e = launch_mid(gx.n, a, p->stream);
+    if (rec) rec->end();
+    if (e) return e;
+  }
+  if (mid_mode == MID_FWD) return cudaSuccess;
+  for (auto& gy : p->groups[1]) {
+    if (gy.n == 1) continue;
+    a.nsub = gy.nsub;
+    memcpy(a.subs, gy.subs, sizeof(a.subs));
+    a.tw = p->tw[gy.n];
+    if (rec) rec->begin(KK_STRIDED_INV);
+    e = launch_strided(gy.n, 1, true, a, p->stream);
+    if (rec) rec->end();
+    if (e) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t run_rows_last(mbs_plan* p, PassArgs a, int mode, bool partials, Recorder* rec) {
+  const int nrb = nrow_blocks(p);
+  a.mode = mode;
+  int poff = 0;
+  for (auto& gz : p->groups[2]) {
+    a.nsub = gz.nsub;
+    memcpy(a.subs, gz.subs, sizeof(a.subs));
+    a.tw = p->tw[gz.n];
+    a.partials = partials ? p->partials + poff : nullptr;
+    poff += nrb * gz.nsub;
+    if (rec) rec->begin(KK_ROWS_LAST);
+    cudaError_t e = launch_rows_last(gz.n, a, nrb, p->stream);
+    if (rec) rec->end();
+    if (e) return e;
+  }
+  return cudaSuccess;
+}
+
+// One iteration of Eq. wavesim_iter on the plan's state (x, source).
+cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
+  cudaError_t e;
+  PassArgs a = base_args(p);
+  a.X = p->x;
+  a.Xout = p->x;
+  a.state = p->state;
+  if (p->have_source) {
+    a.S = p->src;
+    for (int i = 0; i < 6; i++) a.sbox[i] = p->sbox[i];
+  }
+  ShellArgs s = shell_args(p);
+  s.state = p->state;
+  if (p->has_shell) {
+    s.mode = SHELL_CORR_X;
+    s.F = p->x;
+    if (rec) rec->begin(KK_SHELL_CORR);
+    e = launch_shell(s, kShellBlocks, p->stream);
+    if (rec) rec->end();
+    if (e) return e;
+  }
+  e = run_transform_chain(p, a, FIRST_ITER, MID_PROP, rec);
+  if (e) return e;
+  e = run_rows_last(p, a, LAST_ITER, true, rec);
+  if (e) return e;
+  double* pshell = p->partials + p->n_rows_partials;
+  if (p->has_shell) {
+    s.mode = SHELL_FINAL_ITER;
+    s.F = p->K;
+    s.partials = pshell;
+    if (rec) rec->begin(KK_SHELL_FINAL);
+    e = launch_shell(s, kShellBlocks, p->stream);
+    if (rec) rec->end();
+    if (e) return e;
+  }
+  if (rec) rec->begin(KK_FINALIZE);
+  e = launch_finalize(p->state, p->partials, p->n_rows_partials, pshell, p->has_shell ? kShellBlocks : 0, p->history,
+                      p->stream);
+  if (rec) rec->end();
+  return e;
+}
+
+mbs_status ensure_graph(mbs_plan* p) {
+  if (p->graph_ready) return MBS_OK;
+  cudaGraph_t g;
+  CU(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < p->graph_iters && e == cudaSuccess; i++) e = enqueue_iteration(p, nullptr);
+  cudaError_t e2 = cudaStreamEndCapture(p->stream, &g);
+  if (e) return fail(MBS_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+  if (e2) return fail(MBS_ECUDA, std::string("end capture: ") + cudaGetErrorString(e2));
+  e = cudaGraphInstantiate(&p->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e) return fail(MBS_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  p->graph_ready = true;
+  return MBS_OK;
+}
+
+mbs_status read_state(mbs_plan* p, DevState* out) {
+  CU(cudaMemcpyAsync(p->host_state, p->state, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  *out = *p->host_state;
+  return MBS_OK;
+}
+
+// Copy caller data to a device buffer if it lives on the host.
+mbs_status stage_in(mbs_plan* p, const void* src, float2** dev_out, float2** scratch) {
+  if (is_device_ptr(src)) {
+    *dev_out = (float2*)src;
+    return MBS_OK;
+  }
+  if (!*scratch) CU(cudaMalloc((void**)scratch, nvox(p) * sizeof(float2)));
+  CU(cudaMemcpyAsync(*scratch, src, nvox(p) * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+  *dev_out = *scratch;
+  return MBS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mbs_default_options(mbs_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->truncation = 8;
+  o->alpha = 0.75;
+  o->absorb_kappa = 0.5;
+}
+
+const char* mbs_last_error(void) { return g_err.c_str(); }
+
+mbs_status mbs_workspace_bytes(const int64_t shape[3], const int32_t split[3], const mbs_options* opts,
+                               size_t* bytes) {
+  if (!bytes) return fail(MBS_EINVAL, "bytes is null");
+  mbs_plan tmp;
+  const int32_t w[6] = {0, 0, 0, 0, 0, 0};
+  mbs_status s = validate_and_fill(&tmp, shape, 1.0, 1.0, w, split, opts);
+  if (s) return s;
+  build_groups(&tmp);
+  *bytes = layout(&tmp, nullptr, false);
+  return MBS_OK;
+}
+
+mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double pixel_size, double wavelength,
+                           const void* refractive_index, const int32_t boundary_widths[6], const int32_t split[3],
+                           const mbs_options* opts) {
+  g_err.clear();
+  if (!plan_out || !refractive_index) return fail(MBS_EINVAL, "plan and refractive_index are required");
+  *plan_out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(MBS_ECUDA, "no CUDA device");
+  }
+  mbs_plan* p = new mbs_plan();
+  p->stream = nullptr;
+  p->own_stream = false;
+  p->base = nullptr;
+  p->own_base = false;
+  p->tmp_in = p->tmp_out = nullptr;
+  p->graph_ready = false;
+  p->have_source = false;
+  p->host_pinned = nullptr;
+  p->host_state = nullptr;
+  mbs_status st = validate_and_fill(p, shape, pixel_size, wavelength, boundary_widths, split, opts);
+  if (st) {
+    delete p;
+    return st;
+  }
+  build_groups(p);
+  fill_grid_desc(p);
+  if (p->graph_iters == 0) {
+    const double v = (double)nvox(p);
+    p->graph_iters = v >= 8e6 ? 10 : (v >= 1e6 ? 25 : 50);
+  }
+  if (opts && opts->stream) {
+    p->stream = (cudaStream_t)opts->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete p;
+      return fail(MBS_ECUDA, "stream creation failed");
+    }
+    p->own_stream = true;
+  }
+  p->bytes = layout(p, nullptr, false);
+  auto cleanup = [&](mbs_status s) {
+    mbs_plan_destroy(p);
+    return s;
+  };
+  if (opts && opts->workspace) {
+    if (opts->workspace_bytes < p->bytes) return cleanup(fail(MBS_ENOMEM, "workspace too small"));
+    p->base = opts->workspace;
+  } else {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return cleanup(fail(MBS_ECUDA, "cudaMemGetInfo failed"));
+    if (p->bytes > fr) return cleanup(fail(MBS_ENOMEM, "plan needs " + std::to_string(p->bytes) + " bytes, " +
+                                                           std::to_string(fr) + " free"));
+    if (cudaMalloc(&p->base, p->bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p->base = nullptr;
+      return cleanup(fail(MBS_ENOMEM, "cudaMalloc of the plan workspace failed"));
+    }
+    p->own_base = true;
+  }
+  layout(p, (char*)p->base, true);
+  if (cudaMallocHost((void**)&p->host_state, sizeof(DevState)) != cudaSuccess)
+    return cleanup(fail(MBS_ECUDA, "pinned allocation failed"));
+  st = upload_tables(p);
+  if (st) return cleanup(st);
+  // refractive index: use the device array directly, or stage it through src
+  const float2* n_dev = nullptr;
+  if (is_device_ptr(refractive_index)) {
+    n_dev = (const float2*)refractive_index;
+  } else {
+    if (cudaMemcpyAsync(p->src, refractive_index, nvox(p) * sizeof(float2), cudaMemcpyHostToDevice, p->stream) !=
+        cudaSuccess)
+      return cleanup(fail(MBS_ECUDA, "copy of the refractive index failed"));
+    n_dev = p->src;
+  }
+  st = setup_medium(p, n_dev);
+  if (st) return cleanup(st);
+  if (launch_zero(p->x, nvox(p), p->stream) || launch_zero(p->src, nvox(p), p->stream))
+    return cleanup(fail(MBS_ECUDA, "zero fill failed"));
+  if (launch_state_arm(p->state, 0, 0.0, 1, kHistCap, p->stream) ||
+      launch_state_arm(p->free_state, 0, 0.0, 1, kHistCap, p->stream))
+    return cleanup(fail(MBS_ECUDA, "state init failed"));
+  // the operator state is never "done"
+  DevState fs;
+  memset(&fs, 0, sizeof(fs));
+  if (cudaMemcpyAsync(p->free_state, &fs, sizeof(fs), cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+      cudaStreamSynchronize(p->stream) != cudaSuccess)
+    return cleanup(fail(MBS_ECUDA, "state init failed"));
+  *plan_out = p;
+  return MBS_OK;
+}
+
+mbs_status mbs_plan_get_info(const mbs_plan* p, mbs_plan_info* info) {
+  if (!p || !info) return fail(MBS_EINVAL, "null argument");
+  memset(info, 0, sizeof(*info));
+  info->c_re = p->c_re;
+  info->c_im = p->c_im;
+  info->k0sq_re = p->k0_re;
+  info->k0sq_im = p->k0_im;
+  info->contrast = p->contrast;
+  info->block_norm = p->wnorm;
+  info->t = p->t;
+  info->alpha = p->alpha;
+  info->device_bytes = p->bytes;
+  info->graph_iters = p->graph_iters;
+  for (int d = 0; d < 3; d++) {
+    info->a[d] = p->a[d];
+    info->shape[d] = p->N[d];
+    info->split[d] = p->S[d];
+    for (int s = 0; s < p->S[d]; s++) info->sizes[d][s] = p->sizes[d][s];
+  }
+  return MBS_OK;
+}
+
+mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* out) {
+  g_err.clear();
+  if (!p || !x || !out) return fail(MBS_EINVAL, "null argument");
+  if (x == out) return fail(MBS_EINVAL, "x and out must not alias");
+  float2 *xd = nullptr, *od = nullptr;
+  mbs_status st = stage_in(p, x, &xd, &p->tmp_in);
+  if (st) return st;
+  const bool out_dev = is_device_ptr(out);
+  if (out_dev) {
+    od = (float2*)out;
+  } else {
+    if (!p->tmp_out) CU(cudaMalloc((void**)&p->tmp_out, nvox(p) * sizeof(float2)));
+    od = p->tmp_out;
+  }
+  PassArgs a = base_args(p);
+  a.X = xd;
+  a.Xout = od;
+  a.state = p->free_state;
+  ShellArgs s = shell_args(p);
+  s.state = p->free_state;
+  s.out = od;
+  cudaError_t e = cudaSuccess;
+  const int64_t nv = nvox(p);
+  switch (which) {
+    case MBS_OP_A:
+      e = run_transform_chain(p, a, FIRST_PLAIN, MID_LSYM, nullptr);
+      if (!e) e = run_rows_last(p, a, LAST_AOUT, false, nullptr);
+      if (!e && p->has_shell) {
+        s.mode = SHELL_ADD_E;
+        s.F = xd;
+        e = launch_shell(s, kShellBlocks, p->stream);
+      }
+      break;
+    case MBS_OP_PRECOND:
+      if (p->have_source) {
+        a.S = p->src;
+        for (int i = 0; i < 6; i++) a.sbox[i] = p->sbox[i];
+      }
+      if (p->has_shell) {
+        s.mode = SHELL_CORR_X;
+        s.F = xd;
+        e = launch_shell(s, kShellBlocks, p->stream);
+      }
+      if (!e) e = run_transform_chain(p, a, FIRST_ITER, MID_PROP, nullptr);
+      if (!e) e = run_rows_last(p, a, LAST_PRECOND, false, nullptr);
+      if (!e && p->has_shell) {
+        s.mode = SHELL_FINAL_PRECOND;
+        s.F = p->K;
+        e = launch_shell(s, kShellBlocks, p->stream);
+      }
+      break;
+    case MBS_OP_V:
+      e = launch_pointwise_V(xd, p->B, od, nv, p->stream);
+      if (!e && p->has_shell) {
+        s.mode = SHELL_ADD_E;
+        s.F = xd;
+        e = launch_shell(s, kShellBlocks, p->stream);
+      }
+      break;
+    case MBS_OP_E:
+      e = launch_zero(od, nv, p->stream);
+      if (!e && p->has_shell) {
+        s.mode = SHELL_SET_E;
+        s.F = xd;
+        e = launch_shell(s, kShellBlocks, p->stream);
+      }
+      break;
+    case MBS_OP_L:
+      e = run_transform_chain(p, a, FIRST_PLAIN, MID_LSYM, nullptr);
+      if (!e) e = run_rows_last(p, a, LAST_PLAIN, false, nullptr);
+      break;
+    case MBS_OP_PROPAGATE:
+      e = run_transform_chain(p, a, FIRST_PLAIN, MID_PROP, nullptr);
+      if (!e) e = run_rows_last(p, a, LAST_PLAIN, false, nullptr);
+      break;
+    case MBS_OP_FFT:
+      e = run_transform_chain(p, a, FIRST_PLAIN, MID_FWD, nullptr);
+      if (!e) e = cudaMemcpyAsync(od, p->K, nv * sizeof(float2), cudaMemcpyDeviceToDevice, p->stream);
+      break;
+    case MBS_OP_IFFT: {
+      e = cudaMemcpyAsync(p->K, xd, nv * sizeof(float2), cudaMemcpyDeviceToDevice, p->stream);
+      a.mode = MID_INV;
+      for (auto& gx : p->groups[0]) {
+        if (e) break;
+        a.nsub = gx.nsub;
+        memcpy(a.subs, gx.subs, sizeof(a.subs));
+        a.tw = p->tw[gx.n];
+        e = launch_mid(gx.n, a, p->stream);
+      }
+      for (auto& gy : p->groups[1]) {
+        if (e || gy.n == 1) continue;
+        a.nsub = gy.nsub;
+        memcpy(a.subs, gy.subs, sizeof(a.subs));
+        a.tw = p->tw[gy.n];
+        e = launch_strided(gy.n, 1, true, a, p->stream);
+      }
+      if (!e) e = run_rows_last(p, a, LAST_PLAIN, false, nullptr);
+      break;
+    }
+    default:
+      return fail(MBS_EINVAL, "unknown operator");
+  }
+  if (e) return fail(MBS_ECUDA, std::string("operator launch: ") + cudaGetErrorString(e));
+  if (!out_dev) CU(cudaMemcpyAsync(out, od, nv * sizeof(float2), cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  return MBS_OK;
+}
+
+mbs_status mbs_set_source(mbs_plan* p, const void* source) {
+  g_err.clear();
+  if (!p || !source) return fail(MBS_EINVAL, "null argument");
+  const int64_t nv = nvox(p);
+  const cudaMemcpyKind kind = is_device_ptr(source) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CU(cudaMemcpyAsync(p->src, source, nv * sizeof(float2), kind, p->stream));
+  const int init[6] = {INT32_MAX, -1, INT32_MAX, -1, INT32_MAX, -1};
+  CU(cudaMemcpyAsync(p->box_dev, init, sizeof(init), cudaMemcpyHostToDevice, p->stream));
+  CU(launch_source_box(p->src, p->g, p->box_dev, kSetupBlocks, p->stream));
+  int box[6];
+  CU(cudaMemcpyAsync(box, p->box_dev, sizeof(box), cudaMemcpyDeviceToHost, p->stream));
+  CU(launch_zero(p->x, nv, p->stream));
+  CU(launch_state_arm(p->state, 0, 0.0, 1, kHistCap, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  for (int i = 0; i < 6; i++) p->sbox[i] = box[i];
+  if (box[1] < 0) {  // all-zero source: an empty box
+    for (int i = 0; i < 6; i++) p->sbox[i] = 0;
+  }
+  p->have_source = true;
+  if (p->graph_ready) {  // the captured graph holds the source box: capture again
+    cudaGraphExecDestroy(p->graph);
+    p->graph_ready = false;
+  }
+  return MBS_OK;
+}
+
+mbs_status mbs_iterate(mbs_plan* p, int32_t n_iter, double tol, int32_t no_poll, int32_t* iters_done,
+                       double* residual) {
+  g_err.clear();
+  if (!p) return fail(MBS_EINVAL, "null plan");
+  if (n_iter < 0) return fail(MBS_EINVAL, "n_iter must be >= 0");
+  CU(launch_state_arm(p->state, n_iter, tol, 0, kHistCap, p->stream));
+  const bool use_graph = !(p->flags & MBS_FLAG_NO_GRAPH);
+  int remaining = n_iter;
+  DevState hs;
+  if (use_graph && remaining >= p->graph_iters) {
+    mbs_status st = ensure_graph(p);
+    if (st) return st;
+    while (remaining >= p->graph_iters) {
+      CU(cudaGraphLaunch(p->graph, p->stream));
+      remaining -= p->graph_iters;
+      if (!no_poll) {
+        st = read_state(p, &hs);
+        if (st) return st;
+        if (hs.done) {
+          remaining = 0;
+          break;
+        }
+      }
+    }
+  }
+  for (int i = 0; i < remaining; i++) {
+    cudaError_t e = enqueue_iteration(p, nullptr);
+    if (e) return fail(MBS_ECUDA, std::string("iteration launch: ") + cudaGetErrorString(e));
+    if (!no_poll && (i % 64) == 63) {
+      mbs_status st = read_state(p, &hs);
+      if (st) return st;
+      if (hs.done) break;
+    }
+  }
+  mbs_status st = read_state(p, &hs);
+  if (st) return st;
+  if (iters_done) *iters_done = hs.iter;
+  if (residual) *residual = hs.eps;
+  if (hs.status == MBS_ENAN) return fail(MBS_ENAN, "residual is not finite");
+  if (hs.status == MBS_EDIVERGE) return fail(MBS_EDIVERGE, "residual kept rising");
+  if (hs.iter > 0 && hs.eps < tol) return MBS_OK;
+  return MBS_ENOCONV;
+}
+
+mbs_status mbs_get_field(const mbs_plan* p, void* out) {
+  g_err.clear();
+  if (!p || !out) return fail(MBS_EINVAL, "null argument");
+  const cudaMemcpyKind kind = is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CU(cudaMemcpyAsync(out, p->x, nvox(p) * sizeof(float2), kind, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  return MBS_OK;
+}
+
+mbs_status mbs_get_history(const mbs_plan* p, double* history, int32_t cap, int32_t* n_out) {
+  g_err.clear();
+  if (!p) return fail(MBS_EINVAL, "null plan");
+  CU(cudaMemcpyAsync(p->host_state, p->state, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  const int n = std::min(std::min(p->host_state->iter, kHistCap), std::max(cap, 0));
+  if (n > 0 && history) {
+    CU(cudaMemcpyAsync(history, p->history, n * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+  }
+  if (n_out) *n_out = history ? n : std::min(p->host_state->iter, kHistCap);
+  return MBS_OK;
+}
+
+mbs_status mbs_solve(mbs_plan* p, const void* source, void* out, double tol, int32_t max_iter, int32_t* iters_out,
+                     double* residual_out, double* history) {
+  mbs_status st = mbs_set_source(p, source);
+  if (st) return st;
+  int32_t it = 0;
+  double res = 0.0;
+  mbs_status sit = mbs_iterate(p, max_iter, tol, 0, &it, &res);
+  if (sit != MBS_OK && sit != MBS_ENOCONV) return sit;
+  if (iters_out) *iters_out = it;
+  if (residual_out) *residual_out = res;
+  if (history) {
+    int32_t n = 0;
+    st = mbs_get_history(p, history, max_iter, &n);
+    if (st) return st;
+  }
+  st = mbs_get_field(p, out);
+  if (st) return st;
+  if (sit == MBS_ENOCONV) g_err = "max_iter reached before tol";
+  return sit;
+}
+
+const char* mbs_kernel_kind_name(int32_t kind) {
+  static const char* names[MBS_KERNEL_KINDS] = {"shell_corr",  "rows_first", "strided_fwd",  "mid_axis0",
+                                                "strided_inv", "rows_last",  "shell_update", "finalize"};
+  return (kind >= 0 && kind < MBS_KERNEL_KINDS) ? names[kind] : "";
+}
+
+mbs_status mbs_profile_iterations(mbs_plan* p, int32_t n_iter, int32_t launches[MBS_KERNEL_KINDS],
+                                  double ms[MBS_KERNEL_KINDS]) {
+  g_err.clear();
+  if (!p || n_iter < 0) return fail(MBS_EINVAL, "bad argument");
+  for (int k = 0; k < MBS_KERNEL_KINDS; k++) {
+    if (launches) launches[k] = 0;
+    if (ms) ms[k] = 0.0;
+  }
+  CU(launch_state_arm(p->state, n_iter, 0.0, 0, kHistCap, p->stream));
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  Recorder rec;
+  rec.ev = &ev;
+  rec.st = p->stream;
+  for (int i = 0; i < n_iter; i++) {
+    cudaError_t e = enqueue_iteration(p, &rec);
+    if (e) return fail(MBS_ECUDA, std::string("iteration launch: ") + cudaGetErrorString(e));
+  }
+  CU(cudaStreamSynchronize(p->stream));
+  for (auto& it : ev) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, it.second.first, it.second.second);
+    if (launches) launches[it.first] += 1;
+    if (ms) ms[it.first] += t;
+    cudaEventDestroy(it.second.first);
+    cudaEventDestroy(it.second.second);
+  }
+  return MBS_OK;
+}
+
+void mbs_plan_destroy(mbs_plan* p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->graph_ready) cudaGraphExecDestroy(p->graph);
+  if (p->own_base && p->base) cudaFree(p->base);
+  if (p->tmp_in) cudaFree(p->tmp_in);
+  if (p->tmp_out) cudaFree(p->tmp_out);
+  if (p->host_state) cudaFreeHost(p->host_state);
+  if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+  delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,383 @@
+// Edge-correction, residual and set-up kernels of the MBS library.
+#include <math.h>
+
+#include "mbs_fft.cuh"
+#include "mbs_internal.h"
+#include "../../include/mbs.h"
+
+namespace mbs {
+
+// ---------------------------------------------------------------------------
+// Edge corrections (Sec. 3, Figs. 4-5; Sec. 3.1 steps 1-5).
+//
+// For a voxel in the last t layers of subdomain s along axis d (row aa of W):
+//   (E f) += sum_b cW[aa][b] (f_right[b] - f_s[b])        f_.[b]: first t layers
+// for a voxel in the first t layers (row a of W^T):
+//   (E f) += sum_b cW[b][a] (f_left[n-t+b] - f_s[n-t+b])   last t layers
+// with a missing neighbour contributing nothing (wrap removal only). The terms
+// of different axes add. One thread computes the whole correction of one voxel
+// by gathering the 2t inputs per axis (they are re-read from L1/L2 by the
+// neighbouring voxels of the same pencil set).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 corr_axis(const float2* __restrict__ F, long long v, long long stride, int i,
+                                           const AxisDesc& ax, const int* __restrict__ subt,
+                                           const int* __restrict__ loct, const float2* __restrict__ cW, int t) {
+  const int s = __ldg(subt + i), a = __ldg(loct + i), n = ax.n[s];
+  const long long b0 = v - (long long)i * stride;
+  float2 acc = make_float2(0.f, 0.f);
+  if (a >= n - t) {
+    const int aa = a - (n - t);
+    const long long own = b0 + (long long)ax.off[s] * stride;
+    const int rgt = ax.right[s];
+    const long long nb = rgt >= 0 ? b0 + (long long)ax.off[rgt] * stride : 0;
+    for (int b = 0; b < t; b++) {
+      const float2 w = __ldg(cW + aa * t + b);
+      float2 f = F[own + b * stride];
+      f = (rgt >= 0) ? csub(F[nb + b * stride], f) : make_float2(-f.x, -f.y);
+      acc = cadd(acc, cmul(w, f));
+    }
+  }
+  if (a < t) {
+    const long long own = b0 + (long long)(ax.off[s] + n - t) * stride;
+    const int lft = ax.left[s];
+    const long long nb = lft >= 0 ? b0 + (long long)(ax.off[lft] + ax.n[lft] - t) * stride : 0;
+    for (int b = 0; b < t; b++) {
+      const float2 w = __ldg(cW + b * t + a);
+      float2 f = F[own + b * stride];
+      f = (lft >= 0) ? csub(F[nb + b * stride], f) : make_float2(-f.x, -f.y);
+      acc = cadd(acc, cmul(w, f));
+    }
+  }
+  return acc;
+}
+
+__device__ __forceinline__ double block_sum_all(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; i++) s += red[i];
+  return s;
+}
+
+// Shell kernel: one warp per grid row (i0, i1); a row whose i0 or i1 lies in a
+// boundary layer is processed whole, other rows only at the axis-2 layers.
+__global__ void __launch_bounds__(256) k_shell(const __grid_constant__ ShellArgs a) {
+  __shared__ double red[8];
+  if (a.state && a.state->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long N0 = a.g.N0, N1 = a.g.N1, N2 = a.g.N2;
+  const long long rows = N0 * N1;
+  const int t = a.g.t;
+  double acc = 0.0;
+  for (long long rho = (long long)blockIdx.x * 8 + warp; rho < rows; rho += (long long)gridDim.x * 8) {
+    const long long i0 = rho / N1, i1 = rho - i0 * N1;
+    const bool s0 = a.tb.shell[0][i0], s1 = a.tb.shell[1][i1];
+    const bool full = s0 || s1;
+    const long long cnt = full ? N2 : a.tb.nsh2;
+    for (long long k = lane; k < cnt; k += 32) {
+      const long long i2 = full ? k : a.tb.sh2list[k];
+      const long long v = rho * N2 + i2;
+      float2 E = make_float2(0.f, 0.f);
+      if (s0) E = cadd(E, corr_axis(a.F, v, N1 * N2, (int)i0, a.g.ax[0], a.tb.sub[0], a.tb.loc[0], a.cW, t));
+      if (s1) E = cadd(E, corr_axis(a.F, v, N2, (int)i1, a.g.ax[1], a.tb.sub[1], a.tb.loc[1], a.cW, t));
+      if (a.tb.shell[2][i2]) E = cadd(E, corr_axis(a.F, v, 1, (int)i2, a.g.ax[2], a.tb.sub[2], a.tb.loc[2], a.cW, t));
+      switch (a.mode) {
+        case SHELL_CORR_X:
+          a.K[v] = E;
+          break;
+        case SHELL_FINAL_ITER:
+        case SHELL_FINAL_PRECOND: {
+          const float2 ee = a.F[v];
+          const float2 r = csub(cmul(a.B[v], ee), E);
+          acc += (double)r.x * r.x + (double)r.y * r.y;
+          if (a.mode == SHELL_FINAL_ITER) {
+            const float2 x = a.X[v];
+            a.X[v] = make_float2(fmaf(-a.alpha, r.x, x.x), fmaf(-a.alpha, r.y, x.y));
+          } else {
+            a.out[v] = make_float2(-r.x, -r.y);
+          }
+          break;
+        }
+        case SHELL_ADD_E:
+          a.out[v] = cadd(a.out[v], E);
+          break;
+        default:
+          a.out[v] = E;
+          break;
+      }
+    }
+  }
+  if (a.partials) {
+    const double s = block_sum_all(acc, red);
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
+  }
+}
+
+cudaError_t launch_shell(const ShellArgs& a, int blocks, cudaStream_t st) {
+  k_shell<<<blocks, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Deterministic FP64 sum of the per-block partials, relative residual and stop
+// test (Sec. 3.1: eps = ||Gamma^-1 (y - A x_n)|| / ||Gamma^-1 y||, threshold).
+__global__ void __launch_bounds__(1024) k_finalize(DevState* st, const double* __restrict__ p1, int n1,
+                                                   const double* __restrict__ p2, int n2, double* hist) {
+  __shared__ double red[32];
+  if (st->done) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) s += p1[i];
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) s += p2[i];
+  const double R = block_sum_all(s, red);
+  if (threadIdx.x == 0) {
+    const int it = st->iter;
+    if (it == 0) st->R0 = R;
+    const double eps = st->R0 > 0.0 ? sqrt(R / st->R0) : 0.0;
+    if (hist && it < st->hist_cap) hist[it] = eps;
+    st->eps = eps;
+    st->iter = it + 1;
+    if (!isfinite(eps) || !isfinite(R)) {
+      st->status = MBS_ENAN;
+      st->done = 1;
+    } else {
+      if (eps < st->best) {
+        st->best = eps;
+        st->rise = 0;
+      } else if (eps > 4.0 * st->best && eps > 1e-3) {
+        st->rise += 1;
+      } else {
+        st->rise = 0;
+      }
+      if (st->rise >= 20) {
+        st->status = MBS_EDIVERGE;
+        st->done = 1;
+      } else if (eps < st->tol || st->iter >= st->max_iter) {
+        st->done = 1;
+      }
+    }
+  }
+}
+
+cudaError_t launch_finalize(DevState* state, const double* p1, int n1, const double* p2, int n2, double* history,
+                            cudaStream_t st) {
+  k_finalize<<<1, 1024, 0, st>>>(state, p1, n1, p2, n2, history);
+  return cudaGetLastError();
+}
+
+__global__ void k_state_arm(DevState* st, int add_iter, double tol, int reset, int hist_cap) {
+  if (reset) {
+    st->iter = 0;
+    st->R0 = 0.0;
+    st->eps = 1.0;
+    st->best = 1e300;
+    st->rise = 0;
+    st->status = 0;
+    st->hist_cap = hist_cap;
+  }
+  st->max_iter = st->iter + add_iter;
+  st->tol = tol;
+  st->done = (add_iter > 0 && st->status == 0) ? 0 : 1;
+}
+
+cudaError_t launch_state_arm(DevState* state, int add_iter, double tol, int reset, int hist_cap, cudaStream_t st) {
+  k_state_arm<<<1, 1, 0, st>>>(state, add_iter, tol, reset, hist_cap);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Plan set-up in FP64: absorbing ramp, k^2, bounds, contrast and B.
+// ---------------------------------------------------------------------------
+struct Ramp {
+  __device__ static double at(long long i, long long N, int lo, int hi) {
+    double r = 0.0;
+    if (lo > 0 && i < lo) r += (double)(lo - i) / lo;
+    const long long j = N - 1 - i;
+    if (hi > 0 && j < hi) r += (double)(hi - j) / hi;
+    return r;
+  }
+};
+
+__device__ __forceinline__ void k2_at(const float2* n, long long v, const GridDesc& g, const int* w, double kappa,
+                                      double lambda, double& kr, double& ki) {
+  const long long i0 = v / (g.N1 * g.N2), rem = v - i0 * g.N1 * g.N2, i1 = rem / g.N2, i2 = rem - i1 * g.N2;
+  const double ramp = Ramp::at(i0, g.N0, w[0], w[1]) + Ramp::at(i1, g.N1, w[2], w[3]) + Ramp::at(i2, g.N2, w[4], w[5]);
+  const float2 nn = n[v];
+  const double nr = nn.x, ni = (double)nn.y + kappa * ramp;
+  const double s = 2.0 * 3.14159265358979323846 / lambda;
+  const double kr0 = s * nr, ki0 = s * ni;
+  kr = kr0 * kr0 - ki0 * ki0;
+  ki = 2.0 * kr0 * ki0;
+}
+
+struct Widths {
+  int w[6];
+};
+
+// Per-block bounds of k^2 over the grid: min/max of Re and Im, max |k^2| and a
+// count of non-finite values (6 doubles per block).
+__global__ void k_k2_bounds(const float2* __restrict__ n, GridDesc g, Widths w, double kappa, double lambda,
+                            double* partials) {
+  __shared__ double red[6][8];
+  const long long total = g.N0 * g.N1 * g.N2;
+  double v6[6] = {1e300, -1e300, 1e300, -1e300, 0.0, 0.0};
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (long long)gridDim.x * blockDim.x) {
+    double kr, ki;
+    k2_at(n, v, g, w.w, kappa, lambda, kr, ki);
+    if (!(isfinite(kr) && isfinite(ki))) {
+      v6[5] += 1.0;
+      continue;
+    }
+    v6[0] = fmin(v6[0], kr);
+    v6[1] = fmax(v6[1], kr);
+    v6[2] = fmin(v6[2], ki);
+    v6[3] = fmax(v6[3], ki);
+    v6[4] = fmax(v6[4], hypot(kr, ki));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    v6[0] = fmin(v6[0], __shfl_xor_sync(0xffffffffu, v6[0], o));
+    v6[1] = fmax(v6[1], __shfl_xor_sync(0xffffffffu, v6[1], o));
+    v6[2] = fmin(v6[2], __shfl_xor_sync(0xffffffffu, v6[2], o));
+    v6[3] = fmax(v6[3], __shfl_xor_sync(0xffffffffu, v6[3], o));
+    v6[4] = fmax(v6[4], __shfl_xor_sync(0xffffffffu, v6[4], o));
+    v6[5] += __shfl_xor_sync(0xffffffffu, v6[5], o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int k = 0; k < 6; k++) red[k][warp] = v6[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); i++) {
+      v6[0] = fmin(red[0][0], red[0][i]);
+      red[0][0] = v6[0];
+      red[1][0] = fmax(red[1][0], red[1][i]);
+      red[2][0] = fmin(red[2][0], red[2][i]);
+      red[3][0] = fmax(red[3][0], red[3][i]);
+      red[4][0] = fmax(red[4][0], red[4][i]);
+      red[5][0] += red[5][i];
+    }
+    for (int k = 0; k < 6; k++) partials[6 * blockIdx.x + k] = red[k][0];
+  }
+}
+
+cudaError_t launch_k2_bounds(const float2* n, GridDesc g, const int* widths, double kappa, double lambda,
+                             double* partials, int blocks, cudaStream_t st) {
+  Widths w;
+  for (int i = 0; i < 6; i++) w.w[i] = widths[i];
+  k_k2_bounds<<<blocks, 256, 0, st>>>(n, g, w, kappa, lambda, partials);
+  return cudaGetLastError();
+}
+
+__global__ void k_contrast(const float2* __restrict__ n, GridDesc g, Widths w, double kappa, double lambda,
+                           double k0r, double k0i, double* partials) {
+  __shared__ double red[8];
+  const long long total = g.N0 * g.N1 * g.N2;
+  double mx = 0.0;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (long long)gridDim.x * blockDim.x) {
+    double kr, ki;
+    k2_at(n, v, g, w.w, kappa, lambda, kr, ki);
+    mx = fmax(mx, hypot(kr - k0r, ki - k0i));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = red[0];
+    for (int i = 1; i < (int)(blockDim.x >> 5); i++) m = fmax(m, red[i]);
+    partials[blockIdx.x] = m;
+  }
+}
+
+cudaError_t launch_contrast(const float2* n, GridDesc g, const int* widths, double kappa, double lambda,
+                            double k0re, double k0im, double* partials, int blocks, cudaStream_t st) {
+  Widths w;
+  for (int i = 0; i < 6; i++) w.w[i] = widths[i];
+  k_contrast<<<blocks, 256, 0, st>>>(n, g, w, kappa, lambda, k0re, k0im, partials);
+  return cudaGetLastError();
+}
+
+// B = 1 - c (k^2 - k0^2) (Sec. 2: the medium factor I - V of Eq. wavesim_iter),
+// evaluated in FP64 and rounded to complex64. May run in place (B == n).
+__global__ void k_make_B(const float2* n, float2* B, GridDesc g, Widths w, double kappa, double lambda, double k0r,
+                         double k0i, double cr, double ci) {
+  const long long total = g.N0 * g.N1 * g.N2;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (long long)gridDim.x * blockDim.x) {
+    double kr, ki;
+    k2_at(n, v, g, w.w, kappa, lambda, kr, ki);
+    const double dr = kr - k0r, di = ki - k0i;
+    B[v] = make_float2((float)(1.0 - (cr * dr - ci * di)), (float)(-(cr * di + ci * dr)));
+  }
+}
+
+cudaError_t launch_make_B(const float2* n, float2* B, GridDesc g, const int* widths, double kappa, double lambda,
+                          double k0re, double k0im, double cre, double cim, int blocks, cudaStream_t st) {
+  Widths w;
+  for (int i = 0; i < 6; i++) w.w[i] = widths[i];
+  k_make_B<<<blocks, 256, 0, st>>>(n, B, g, w, kappa, lambda, k0re, k0im, cre, cim);
+  return cudaGetLastError();
+}
+
+// Bounding box of the non-zero source voxels (atomic min/max of the indices).
+__global__ void k_source_box(const float2* __restrict__ S, GridDesc g, int* box) {
+  const long long total = g.N0 * g.N1 * g.N2;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (long long)gridDim.x * blockDim.x) {
+    const float2 s = S[v];
+    if (s.x != 0.f || s.y != 0.f) {
+      const long long i0 = v / (g.N1 * g.N2), rem = v - i0 * g.N1 * g.N2, i1 = rem / g.N2, i2 = rem - i1 * g.N2;
+      atomicMin(box + 0, (int)i0);
+      atomicMax(box + 1, (int)i0 + 1);
+      atomicMin(box + 2, (int)i1);
+      atomicMax(box + 3, (int)i1 + 1);
+      atomicMin(box + 4, (int)i2);
+      atomicMax(box + 5, (int)i2 + 1);
+    }
+  }
+}
+
+cudaError_t launch_source_box(const float2* S, GridDesc g, int* box, int blocks, cudaStream_t st) {
+  k_source_box<<<blocks, 256, 0, st>>>(S, g, box);
+  return cudaGetLastError();
+}
+
+__global__ void k_zero(float2* p, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = make_float2(0.f, 0.f);
+}
+
+cudaError_t launch_zero(float2* p, int64_t n, cudaStream_t st) {
+  const long long blocks = n / 256 + 1 < 152 * 16 ? n / 256 + 1 : 152 * 16;
+  k_zero<<<(unsigned)blocks, 256, 0, st>>>(p, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_negate_copy(const float2* __restrict__ in, float2* out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = in[i];
+    out[i] = make_float2(-v.x, -v.y);
+  }
+}
+
+cudaError_t launch_negate_copy(const float2* in, float2* out, int64_t n, cudaStream_t st) {
+  const long long blocks = n / 256 + 1 < 152 * 16 ? n / 256 + 1 : 152 * 16;
+  k_negate_copy<<<(unsigned)blocks, 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+// out = (1 - B) x = c (k^2 - k0^2) x, the potential part of V.
+__global__ void k_pointwise_V(const float2* __restrict__ X, const float2* __restrict__ B, float2* out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 b = B[i];
+    out[i] = cmul(make_float2(1.f - b.x, -b.y), X[i]);
+  }
+}
+
+cudaError_t launch_pointwise_V(const float2* X, const float2* B, float2* out, int64_t n, cudaStream_t st) {
+  const long long blocks = n / 256 + 1 < 152 * 16 ? n / 256 + 1 : 152 * 16;
+  k_pointwise_V<<<(unsigned)blocks, 256, 0, st>>>(X, B, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace mbs

@@ -1,0 +1,122 @@
+// Internal declarations shared by the CUDA translation units of the MBS library.
+// Nothing here is part of the C ABI (see include/mbs.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mbs {
+
+constexpr int kMaxSplit = 16;   // subdomains per axis
+constexpr int kMaxT = 32;       // truncation width t
+constexpr int kMaxFFT = 512;    // longest subdomain edge handled by the FFT engine
+
+// One axis of the block decomposition (Sec. 3: subdomains along any axis, of
+// unequal sizes). Neighbour -1 means none.
+struct AxisDesc {
+  int N;   // global extent
+  int S;   // subdomains along the axis
+  int a;   // a_d of Eq. c_scale2 (0: no corrections, 1: wrap removal, 2: + transfer)
+  int off[kMaxSplit];
+  int n[kMaxSplit];
+  int left[kMaxSplit];
+  int right[kMaxSplit];
+};
+
+struct GridDesc {
+  int64_t N0, N1, N2;
+  int t;
+  AxisDesc ax[3];
+};
+
+// Per-axis tables over the global index along that axis.
+struct AxisTables {
+  const float* p2[3];     // |p_d|^2 of the subdomain containing the index, FFT order
+  const float* invn[3];   // 1 / n_d of that subdomain
+  const int* sub[3];      // subdomain index
+  const int* loc[3];      // local index inside the subdomain
+  const unsigned char* shell[3];  // 1 if a_d >= 1 and the voxel lies in the first/last t layers
+  const int* sh2list;     // global axis-2 indices with shell[2] set
+  int nsh2;
+};
+
+// Device-side solver state (one per plan). Every iteration kernel leaves at once
+// when `done` is set, so a captured graph can hold more iterations than needed.
+struct DevState {
+  int iter;       // completed updates
+  int max_iter;   // stop when iter reaches this
+  int done;
+  int status;     // 0, or MBS_ENAN / MBS_EDIVERGE
+  double tol;
+  double R0;      // ||r_0||^2
+  double eps;     // last relative residual
+  double best;    // smallest eps so far (divergence guard)
+  int rise;       // consecutive iterations with eps > 2 * best
+  int hist_cap;
+};
+
+enum FirstMode { FIRST_PLAIN = 0, FIRST_ITER = 1 };
+enum LastMode { LAST_PLAIN = 0, LAST_ITER = 1, LAST_PRECOND = 2, LAST_AOUT = 3 };
+enum MidMode { MID_PROP = 0, MID_LSYM = 1, MID_FWD = 2, MID_INV = 3 };
+enum ShellMode { SHELL_CORR_X = 0, SHELL_FINAL_ITER = 1, SHELL_FINAL_PRECOND = 2, SHELL_ADD_E = 3, SHELL_SET_E = 4 };
+
+struct PassArgs {
+  float2* K;            // FFT buffer
+  const float2* X;      // field input
+  float2* Xout;         // updated field or operator output
+  const float2* B;      // medium factor 1 - c(k^2 - k0^2)
+  const float2* S;      // source map (may be null)
+  int64_t sbox[6];      // [lo0, hi0, lo1, hi1, lo2, hi2) support of S
+  float2 mc;            // -c  (y = -c S, Eq. LV)
+  float2 c;             // c
+  float2 ck0;           // c * k0^2
+  float alpha;
+  const float2* tw;     // twiddles exp(-2 pi i k / N), k < N
+  AxisTables tb;
+  GridDesc g;
+  double* partials;     // per-block FP64 partial sums of |r|^2
+  const DevState* state;
+  int mode;
+  int nsub;             // subdomains (along the pass axis) of this size
+  int subs[kMaxSplit];
+};
+
+struct ShellArgs {
+  const float2* F;      // field the corrections are taken of
+  float2* K;            // FFT buffer
+  float2* X;            // field (updated in FINAL_ITER)
+  float2* out;          // operator output
+  const float2* B;
+  const float2* cW;     // c * W, t x t, row-major
+  float alpha;
+  AxisTables tb;
+  GridDesc g;
+  double* partials;
+  const DevState* state;
+  int mode;
+};
+
+// Launchers (return cudaGetLastError of the launch).
+cudaError_t launch_rows_first(int n, const PassArgs& a, int nrows_blocks, cudaStream_t st);
+cudaError_t launch_rows_last(int n, const PassArgs& a, int nrows_blocks, cudaStream_t st);
+cudaError_t launch_strided(int n, int axis, bool inv, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_mid(int n, const PassArgs& a, cudaStream_t st);
+bool fft_size_compiled(int n);
+
+cudaError_t launch_shell(const ShellArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_finalize(DevState* state, const double* p1, int n1, const double* p2, int n2, double* history,
+                            cudaStream_t st);
+cudaError_t launch_state_arm(DevState* state, int add_iter, double tol, int reset, int hist_cap, cudaStream_t st);
+
+// Plan set-up kernels (FP64 arithmetic on the device).
+cudaError_t launch_k2_bounds(const float2* n, GridDesc g, const int* widths, double kappa, double lambda,
+                             double* partials, int blocks, cudaStream_t st);
+cudaError_t launch_contrast(const float2* n, GridDesc g, const int* widths, double kappa, double lambda,
+                            double k0re, double k0im, double* partials, int blocks, cudaStream_t st);
+cudaError_t launch_make_B(const float2* n, float2* B, GridDesc g, const int* widths, double kappa, double lambda,
+                          double k0re, double k0im, double cre, double cim, int blocks, cudaStream_t st);
+cudaError_t launch_source_box(const float2* S, GridDesc g, int* box, int blocks, cudaStream_t st);
+cudaError_t launch_zero(float2* p, int64_t n, cudaStream_t st);
+cudaError_t launch_negate_copy(const float2* in, float2* out, int64_t n, cudaStream_t st);
+cudaError_t launch_pointwise_V(const float2* X, const float2* B, float2* out, int64_t n, cudaStream_t st);
+
+}  // namespace mbs

@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every symbol include/mbs.h declares
+(no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "mbs.h")).read()
+    return sorted(set(re.findall(r"MBS_API\s+[\w\s\*]+?\b(mbs_\w+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2410_02395_gb300 as pkg
+
+    pkg.build()
+    return pkg.load_library()
+
+
+def test_header_declares_the_paper_calls():
+    syms = _declared_symbols()
+    for s in ("mbs_plan_create", "mbs_apply_operator", "mbs_solve", "mbs_plan_destroy", "mbs_last_error"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for s in _declared_symbols():
+        assert hasattr(lib, s), s
+
+
+def test_no_device_gives_error_status_not_fallback(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import numpy as np
+
+    import paper_2410_02395_gb300 as pkg
+
+    with pytest.raises(pkg.MBSError) as ei:
+        pkg.Plan((8, 8, 8), 0.25, 1.0, np.ones((8, 8, 8), np.complex64))
+    assert ei.value.status == 3  # MBS_ECUDA
+
+
+def test_workspace_query_and_validation(lib):
+    import paper_2410_02395_gb300 as pkg
+
+    b1 = pkg.Plan.workspace_bytes((64, 64, 64), (1, 1, 1))
+    b2 = pkg.Plan.workspace_bytes((256, 256, 256), (2, 2, 2))
+    assert b2 > 4 * 256 ** 3 * 8 and b1 > 4 * 64 ** 3 * 8
+    with pytest.raises(pkg.MBSError) as ei:
+        pkg.Plan.workspace_bytes((64, 64, 64), (1, 1, 17))
+    assert ei.value.status == 1
+    with pytest.raises(pkg.MBSError) as ei:
+        pkg.Plan.workspace_bytes((22, 8, 8), (1, 1, 1))      # 22 = 2 * 11: not a compiled FFT length
+    assert ei.value.status == 8
+    with pytest.raises(pkg.MBSError) as ei:
+        pkg.Plan.workspace_bytes((12, 8, 8), (2, 1, 1), truncation=7)   # t > subdomain edge 6
+    assert ei.value.status == 1
+    with pytest.raises(pkg.MBSError):
+        pkg.Plan.workspace_bytes((12, 8, 8), (2, 1, 1), split_sizes=[[5, 6], [8], [8]])
