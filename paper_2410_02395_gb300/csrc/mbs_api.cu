@@ -127,7 +127,9 @@ struct mbs_plan {
   float2* tmp_in;
   float2* tmp_out;
   float *p2[3], *invn[3];
-  int *sub[3], *loc[3], *sh2list;
+  int *sub[3], *loc[3], *sh2list, *kf[3], *kl[3];
+  float2* slab[3];
+  int Wd[3];
   unsigned char* shell[3];
   int nsh2;
   float2* cW;
@@ -185,13 +187,19 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
   char* pB = take(F);
   char* pK = take(F);
   char* psrc = take(F);
-  char *pp2[3], *pinv[3], *psub[3], *ploc[3], *psh[3];
+  char *pp2[3], *pinv[3], *psub[3], *ploc[3], *psh[3], *pkf[3], *pkl[3], *pslab[3];
   for (int d = 0; d < 3; d++) {
     pp2[d] = take(p->N[d] * sizeof(float));
     pinv[d] = take(p->N[d] * sizeof(float));
     psub[d] = take(p->N[d] * sizeof(int));
     ploc[d] = take(p->N[d] * sizeof(int));
     psh[d] = take(p->N[d]);
+    pkf[d] = take(p->N[d] * sizeof(int));
+    pkl[d] = take(p->N[d] * sizeof(int));
+    // correction slab of axis d: S_d * 2t layers times the two other extents
+    const int64_t other = nvox(p) / p->N[d];
+    const bool corr = p->t > 0 && p->a[d] > 0;
+    pslab[d] = corr ? take((size_t)p->S[d] * 2 * p->t * other * sizeof(float2)) : nullptr;
   }
   char* psh2 = take(p->N[2] * sizeof(int));
   char* pcw = take(std::max(1, p->t * p->t) * sizeof(float2));
@@ -219,6 +227,10 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
       p->sub[d] = (int*)psub[d];
       p->loc[d] = (int*)ploc[d];
       p->shell[d] = (unsigned char*)psh[d];
+      p->kf[d] = (int*)pkf[d];
+      p->kl[d] = (int*)pkl[d];
+      p->slab[d] = (float2*)pslab[d];
+      p->Wd[d] = p->S[d] * 2 * p->t;
     }
     p->sh2list = (int*)psh2;
     p->cW = (float2*)pcw;
@@ -327,6 +339,8 @@ mbs_status upload_tables(mbs_plan* p) {
     std::vector<float> p2(N), invn(N);
     std::vector<int> sub(N), loc(N);
     std::vector<unsigned char> sh(N);
+    std::vector<int> kf(N, -1), kl(N, -1);
+    const int t = p->t;
     for (int s = 0; s < p->S[d]; s++) {
       const int n = p->sizes[d][s], o = p->offs[d][s];
       for (int q = 0; q < n; q++) {
@@ -336,9 +350,14 @@ mbs_status upload_tables(mbs_plan* p) {
         invn[o + q] = (float)(1.0 / n);
         sub[o + q] = s;
         loc[o + q] = q;
-        sh[o + q] = (p->t > 0 && p->a[d] > 0 && (q < p->t || q >= n - p->t)) ? 1 : 0;
+        const bool corr = t > 0 && p->a[d] > 0;
+        sh[o + q] = (corr && (q < t || q >= n - t)) ? 1 : 0;
+        if (corr && q < t) kf[o + q] = s * 2 * t + q;
+        if (corr && q >= n - t) kl[o + q] = s * 2 * t + t + (q - (n - t));
       }
     }
+    CU(cudaMemcpyAsync(p->kf[d], kf.data(), N * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+    CU(cudaMemcpyAsync(p->kl[d], kl.data(), N * sizeof(int), cudaMemcpyHostToDevice, p->stream));
     CU(cudaMemcpyAsync(p->p2[d], p2.data(), N * sizeof(float), cudaMemcpyHostToDevice, p->stream));
     CU(cudaMemcpyAsync(p->invn[d], invn.data(), N * sizeof(float), cudaMemcpyHostToDevice, p->stream));
     CU(cudaMemcpyAsync(p->sub[d], sub.data(), N * sizeof(int), cudaMemcpyHostToDevice, p->stream));
@@ -372,6 +391,10 @@ mbs_status upload_tables(mbs_plan* p) {
     tb.sub[d] = p->sub[d];
     tb.loc[d] = p->loc[d];
     tb.shell[d] = p->shell[d];
+    tb.kf[d] = p->kf[d];
+    tb.kl[d] = p->kl[d];
+    tb.C[d] = p->slab[d];
+    tb.Wd[d] = p->Wd[d];
   }
   tb.sh2list = p->sh2list;
   tb.nsh2 = p->nsh2;
@@ -442,20 +465,23 @@ PassArgs base_args(mbs_plan* p) {
 ShellArgs shell_args(mbs_plan* p) {
   ShellArgs s;
   memset(&s, 0, sizeof(s));
-  s.K = p->K;
+  s.E = p->K;
   s.X = p->x;
   s.B = p->B;
-  s.cW = p->cW;
   s.alpha = (float)p->alpha;
   s.tb = p->tb;
   s.g = p->g;
   return s;
 }
 
+// Edge corrections of field F along every corrected axis into the slabs.
+cudaError_t run_corr(mbs_plan* p, const float2* F, const DevState* state);
+
 int nrow_blocks(const mbs_plan* p) { return (int)((p->N[0] * p->N[1] + 31) / 32); }
 
 // Kernel kinds for profiling.
-enum { KK_SHELL_CORR = 0, KK_ROWS_FIRST, KK_STRIDED_FWD, KK_MID, KK_STRIDED_INV, KK_ROWS_LAST, KK_SHELL_FINAL, KK_FINALIZE };
+enum { KK_CORR_X = 0, KK_ROWS_FIRST, KK_STRIDED_FWD, KK_MID, KK_STRIDED_INV, KK_ROWS_LAST, KK_CORR_E, KK_SHELL_UPDATE,
+       KK_FINALIZE };
 
 struct Recorder {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>* ev = nullptr;
@@ -475,6 +501,29 @@ struct Recorder {
     cudaEventRecord(ev->back().second.second, st);
   }
 };
+
+cudaError_t run_corr_rec(mbs_plan* p, const float2* F, const DevState* state, Recorder* rec, int kind) {
+  CorrArgs c;
+  memset(&c, 0, sizeof(c));
+  c.F = F;
+  c.cW = p->cW;
+  c.tb = p->tb;
+  c.g = p->g;
+  c.state = state;
+  for (int d = 0; d < 3; d++) {
+    if (!(p->t > 0 && p->a[d] > 0)) continue;
+    c.axis = d;
+    if (rec) rec->begin(kind);
+    cudaError_t e = launch_corr(c, p->stream);
+    if (rec) rec->end();
+    if (e) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t run_corr(mbs_plan* p, const float2* F, const DevState* state) {
+  return run_corr_rec(p, F, state, nullptr, 0);
+}
 
 // The forward half shared by the iteration and several operators:
 // rows_first (mode), strided axis-1 forward, mid (mode), strided axis-1 inverse.
@@ -554,14 +603,8 @@ cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
     a.S = p->src;
     for (int i = 0; i < 6; i++) a.sbox[i] = p->sbox[i];
   }
-  ShellArgs s = shell_args(p);
-  s.state = p->state;
-  if (p->has_shell) {
-    s.mode = SHELL_CORR_X;
-    s.F = p->x;
-    if (rec) rec->begin(KK_SHELL_CORR);
-    e = launch_shell(s, kShellBlocks, p->stream);
-    if (rec) rec->end();
+  if (p->has_shell) {  // V #1: E x into the slabs (steps 1-2)
+    e = run_corr_rec(p, p->x, p->state, rec, KK_CORR_X);
     if (e) return e;
   }
   e = run_transform_chain(p, a, FIRST_ITER, MID_PROP, rec);
@@ -569,11 +612,14 @@ cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
   e = run_rows_last(p, a, LAST_ITER, true, rec);
   if (e) return e;
   double* pshell = p->partials + p->n_rows_partials;
-  if (p->has_shell) {
-    s.mode = SHELL_FINAL_ITER;
-    s.F = p->K;
+  if (p->has_shell) {  // V #2 on e = x - w: E e, then the layer voxels' update
+    e = run_corr_rec(p, p->K, p->state, rec, KK_CORR_E);
+    if (e) return e;
+    ShellArgs s = shell_args(p);
+    s.state = p->state;
+    s.mode = SHELL_UPDATE_ITER;
     s.partials = pshell;
-    if (rec) rec->begin(KK_SHELL_FINAL);
+    if (rec) rec->begin(KK_SHELL_UPDATE);
     e = launch_shell(s, kShellBlocks, p->stream);
     if (rec) rec->end();
     if (e) return e;
@@ -789,9 +835,9 @@ mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* o
       e = run_transform_chain(p, a, FIRST_PLAIN, MID_LSYM, nullptr);
       if (!e) e = run_rows_last(p, a, LAST_AOUT, false, nullptr);
       if (!e && p->has_shell) {
+        e = run_corr(p, xd, p->free_state);
         s.mode = SHELL_ADD_E;
-        s.F = xd;
-        e = launch_shell(s, kShellBlocks, p->stream);
+        if (!e) e = launch_shell(s, kShellBlocks, p->stream);
       }
       break;
     case MBS_OP_PRECOND:
@@ -799,33 +845,29 @@ mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* o
         a.S = p->src;
         for (int i = 0; i < 6; i++) a.sbox[i] = p->sbox[i];
       }
-      if (p->has_shell) {
-        s.mode = SHELL_CORR_X;
-        s.F = xd;
-        e = launch_shell(s, kShellBlocks, p->stream);
-      }
+      if (p->has_shell) e = run_corr(p, xd, p->free_state);
       if (!e) e = run_transform_chain(p, a, FIRST_ITER, MID_PROP, nullptr);
       if (!e) e = run_rows_last(p, a, LAST_PRECOND, false, nullptr);
       if (!e && p->has_shell) {
-        s.mode = SHELL_FINAL_PRECOND;
-        s.F = p->K;
-        e = launch_shell(s, kShellBlocks, p->stream);
+        e = run_corr(p, p->K, p->free_state);
+        s.mode = SHELL_UPDATE_PRECOND;
+        if (!e) e = launch_shell(s, kShellBlocks, p->stream);
       }
       break;
     case MBS_OP_V:
       e = launch_pointwise_V(xd, p->B, od, nv, p->stream);
       if (!e && p->has_shell) {
+        e = run_corr(p, xd, p->free_state);
         s.mode = SHELL_ADD_E;
-        s.F = xd;
-        e = launch_shell(s, kShellBlocks, p->stream);
+        if (!e) e = launch_shell(s, kShellBlocks, p->stream);
       }
       break;
     case MBS_OP_E:
       e = launch_zero(od, nv, p->stream);
       if (!e && p->has_shell) {
+        e = run_corr(p, xd, p->free_state);
         s.mode = SHELL_SET_E;
-        s.F = xd;
-        e = launch_shell(s, kShellBlocks, p->stream);
+        if (!e) e = launch_shell(s, kShellBlocks, p->stream);
       }
       break;
     case MBS_OP_L:
@@ -984,8 +1026,8 @@ mbs_status mbs_solve(mbs_plan* p, const void* source, void* out, double tol, int
 }
 
 const char* mbs_kernel_kind_name(int32_t kind) {
-  static const char* names[MBS_KERNEL_KINDS] = {"shell_corr",  "rows_first", "strided_fwd",  "mid_axis0",
-                                                "strided_inv", "rows_last",  "shell_update", "finalize"};
+  static const char* names[MBS_KERNEL_KINDS] = {"corr_x",    "rows_first", "strided_fwd",  "mid_axis0", "strided_inv",
+                                                "rows_last", "corr_e",     "shell_update", "finalize"};
   return (kind >= 0 && kind < MBS_KERNEL_KINDS) ? names[kind] : "";
 }
 

@@ -3,6 +3,7 @@
 
 #include "mbs_fft.cuh"
 #include "mbs_internal.h"
+#include "mbs_slab.cuh"
 #include "../../include/mbs.h"
 
 namespace mbs {
@@ -10,45 +11,100 @@ namespace mbs {
 // ---------------------------------------------------------------------------
 // Edge corrections (Sec. 3, Figs. 4-5; Sec. 3.1 steps 1-5).
 //
-// For a voxel in the last t layers of subdomain s along axis d (row aa of W):
-//   (E f) += sum_b cW[aa][b] (f_right[b] - f_s[b])        f_.[b]: first t layers
-// for a voxel in the first t layers (row a of W^T):
-//   (E f) += sum_b cW[b][a] (f_left[n-t+b] - f_s[n-t+b])   last t layers
-// with a missing neighbour contributing nothing (wrap removal only). The terms
-// of different axes add. One thread computes the whole correction of one voxel
-// by gathering the 2t inputs per axis (they are re-read from L1/L2 by the
-// neighbouring voxels of the same pencil set).
+// For every pencil along a corrected axis d and every subdomain s on it, with
+// f_s[b] the b-th voxel of s along the pencil (n = its size):
+//   last t layers  (row a of W):   (E f)_s[n-t+a] = sum_b cW[a][b] (f_right[b]      - f_s[b])
+//   first t layers (row a of W^T): (E f)_s[a]     = sum_b cW[b][a] (f_left[n_l-t+b] - f_s[n-t+b])
+// A missing neighbour contributes nothing (wrap removal only, step 4); a present
+// one adds its transfer (step 5). One thread per (pencil, subdomain) loads the
+// 4t inputs once, keeps the differences in registers and writes the 2t outputs
+// into the axis's slab; the terms of different axes are added by the consumers.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 corr_axis(const float2* __restrict__ F, long long v, long long stride, int i,
-                                           const AxisDesc& ax, const int* __restrict__ subt,
-                                           const int* __restrict__ loct, const float2* __restrict__ cW, int t) {
-  const int s = __ldg(subt + i), a = __ldg(loct + i), n = ax.n[s];
-  const long long b0 = v - (long long)i * stride;
-  float2 acc = make_float2(0.f, 0.f);
-  if (a >= n - t) {
-    const int aa = a - (n - t);
-    const long long own = b0 + (long long)ax.off[s] * stride;
-    const int rgt = ax.right[s];
-    const long long nb = rgt >= 0 ? b0 + (long long)ax.off[rgt] * stride : 0;
-    for (int b = 0; b < t; b++) {
-      const float2 w = __ldg(cW + aa * t + b);
-      float2 f = F[own + b * stride];
-      f = (rgt >= 0) ? csub(F[nb + b * stride], f) : make_float2(-f.x, -f.y);
-      acc = cadd(acc, cmul(w, f));
+template <int TM>
+__global__ void __launch_bounds__(128) k_corr(const __grid_constant__ CorrArgs a) {
+  if (a.state && a.state->done) return;
+  const int d = a.axis;
+  const AxisDesc& ax = a.g.ax[d];
+  const long long N0 = a.g.N0, N1 = a.g.N1, N2 = a.g.N2;
+  const int t = a.g.t, Wd = a.tb.Wd[d];
+  const long long npen = d == 0 ? N1 * N2 : (d == 1 ? N0 * N2 : N0 * N1);
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= npen * ax.S) return;
+  const int s = (int)(gid / npen);
+  const long long p = gid - (long long)s * npen;
+  long long base, stride;
+  if (d == 0) {
+    base = p;
+    stride = N1 * N2;
+  } else if (d == 1) {
+    const long long i0 = p / N2, i2 = p - i0 * N2;
+    base = i0 * N1 * N2 + i2;
+    stride = N2;
+  } else {
+    base = p * N2;
+    stride = 1;
+  }
+  const int off = ax.off[s], n = ax.n[s];
+  const int L = ax.left[s], R = ax.right[s];
+  const float2* __restrict__ F = a.F;
+  float2 D[TM], E[TM];
+#pragma unroll
+  for (int b = 0; b < TM; b++) {
+    if (b < t) {
+      const float2 A = F[base + (long long)(off + b) * stride];
+      const float2 Z = F[base + (long long)(off + n - t + b) * stride];
+      const float2 Rv = R >= 0 ? F[base + (long long)(ax.off[R] + b) * stride] : make_float2(0.f, 0.f);
+      const float2 Lv = L >= 0 ? F[base + (long long)(ax.off[L] + ax.n[L] - t + b) * stride] : make_float2(0.f, 0.f);
+      D[b] = csub(Rv, A);
+      E[b] = csub(Lv, Z);
+    } else {
+      D[b] = E[b] = make_float2(0.f, 0.f);
     }
   }
-  if (a < t) {
-    const long long own = b0 + (long long)(ax.off[s] + n - t) * stride;
-    const int lft = ax.left[s];
-    const long long nb = lft >= 0 ? b0 + (long long)(ax.off[lft] + ax.n[lft] - t) * stride : 0;
-    for (int b = 0; b < t; b++) {
-      const float2 w = __ldg(cW + b * t + a);
-      float2 f = F[own + b * stride];
-      f = (lft >= 0) ? csub(F[nb + b * stride], f) : make_float2(-f.x, -f.y);
-      acc = cadd(acc, cmul(w, f));
+  float2* C = a.tb.C[d];
+  const float2* __restrict__ cW = a.cW;
+#pragma unroll
+  for (int aa = 0; aa < TM; aa++) {
+    if (aa < t) {
+      float2 af = make_float2(0.f, 0.f), al = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < TM; b++) {
+        if (b < t) {
+          af = cadd(af, cmul(__ldg(cW + b * t + aa), E[b]));
+          al = cadd(al, cmul(__ldg(cW + aa * t + b), D[b]));
+        }
+      }
+      const int kf = s * 2 * t + aa, kl = s * 2 * t + t + aa;
+      if (d == 0) {
+        C[(long long)kf * N1 * N2 + p] = af;
+        C[(long long)kl * N1 * N2 + p] = al;
+      } else if (d == 1) {
+        const long long i0 = p / N2, i2 = p - i0 * N2;
+        C[(i0 * Wd + kf) * N2 + i2] = af;
+        C[(i0 * Wd + kl) * N2 + i2] = al;
+      } else {
+        C[p * Wd + kf] = af;
+        C[p * Wd + kl] = al;
+      }
     }
   }
-  return acc;
+}
+
+cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st) {
+  const AxisDesc& ax = a.g.ax[a.axis];
+  const long long npen = a.axis == 0 ? a.g.N1 * a.g.N2 : (a.axis == 1 ? a.g.N0 * a.g.N2 : a.g.N0 * a.g.N1);
+  const long long nth = npen * ax.S;
+  const unsigned blocks = (unsigned)((nth + 127) / 128);
+  const int t = a.g.t;
+  if (t <= 4)
+    k_corr<4><<<blocks, 128, 0, st>>>(a);
+  else if (t <= 8)
+    k_corr<8><<<blocks, 128, 0, st>>>(a);
+  else if (t <= 16)
+    k_corr<16><<<blocks, 128, 0, st>>>(a);
+  else
+    k_corr<32><<<blocks, 128, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 __device__ __forceinline__ double block_sum_all(double v, double* red) {
@@ -63,38 +119,35 @@ __device__ __forceinline__ double block_sum_all(double v, double* red) {
   return s;
 }
 
-// Shell kernel: one warp per grid row (i0, i1); a row whose i0 or i1 lies in a
-// boundary layer is processed whole, other rows only at the axis-2 layers.
+// Boundary-layer voxels: one warp per grid row (i0, i1); a row inside an
+// axis-0/1 layer is processed whole, other rows only at the axis-2 layers.
+// E = sum of the slabs at the voxel, then per mode:
+//   UPDATE_ITER:    r = B e - E, x <- x - alpha r, FP64 |r|^2   (e from the last pass)
+//   UPDATE_PRECOND: out = -(B e - E)
+//   ADD_E:          out += E          SET_E: out = E
 __global__ void __launch_bounds__(256) k_shell(const __grid_constant__ ShellArgs a) {
   __shared__ double red[8];
   if (a.state && a.state->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long N0 = a.g.N0, N1 = a.g.N1, N2 = a.g.N2;
-  const long long rows = N0 * N1;
-  const int t = a.g.t;
+  const long long N1 = a.g.N1, N2 = a.g.N2;
+  const long long rows = a.g.N0 * N1;
   double acc = 0.0;
   for (long long rho = (long long)blockIdx.x * 8 + warp; rho < rows; rho += (long long)gridDim.x * 8) {
     const long long i0 = rho / N1, i1 = rho - i0 * N1;
-    const bool s0 = a.tb.shell[0][i0], s1 = a.tb.shell[1][i1];
-    const bool full = s0 || s1;
+    const bool full = a.tb.shell[0][i0] || a.tb.shell[1][i1];
     const long long cnt = full ? N2 : a.tb.nsh2;
+    if (cnt == 0) continue;
+    const RowSlab rs = row_slab(a.tb, i0, i1);
     for (long long k = lane; k < cnt; k += 32) {
       const long long i2 = full ? k : a.tb.sh2list[k];
       const long long v = rho * N2 + i2;
-      float2 E = make_float2(0.f, 0.f);
-      if (s0) E = cadd(E, corr_axis(a.F, v, N1 * N2, (int)i0, a.g.ax[0], a.tb.sub[0], a.tb.loc[0], a.cW, t));
-      if (s1) E = cadd(E, corr_axis(a.F, v, N2, (int)i1, a.g.ax[1], a.tb.sub[1], a.tb.loc[1], a.cW, t));
-      if (a.tb.shell[2][i2]) E = cadd(E, corr_axis(a.F, v, 1, (int)i2, a.g.ax[2], a.tb.sub[2], a.tb.loc[2], a.cW, t));
+      const float2 E = slab_sum(a.tb, a.g, rs, i0, i1, rho, i2);
       switch (a.mode) {
-        case SHELL_CORR_X:
-          a.K[v] = E;
-          break;
-        case SHELL_FINAL_ITER:
-        case SHELL_FINAL_PRECOND: {
-          const float2 ee = a.F[v];
-          const float2 r = csub(cmul(a.B[v], ee), E);
+        case SHELL_UPDATE_ITER:
+        case SHELL_UPDATE_PRECOND: {
+          const float2 r = csub(cmul(a.B[v], a.E[v]), E);
           acc += (double)r.x * r.x + (double)r.y * r.y;
-          if (a.mode == SHELL_FINAL_ITER) {
+          if (a.mode == SHELL_UPDATE_ITER) {
             const float2 x = a.X[v];
             a.X[v] = make_float2(fmaf(-a.alpha, r.x, x.x), fmaf(-a.alpha, r.y, x.y));
           } else {

@@ -37,6 +37,14 @@ struct AxisTables {
   const unsigned char* shell[3];  // 1 if a_d >= 1 and the voxel lies in the first/last t layers
   const int* sh2list;     // global axis-2 indices with shell[2] set
   int nsh2;
+  // Edge-correction slabs: for axis d the corrections of the first t and last t
+  // layers of every subdomain, slab row k = s*2t + a (first t) or s*2t + t + a
+  // (last t). kf/kl give that row for a global index (-1 if none).
+  //   C[0]: [W0][N1][N2]   C[1]: [N0][W1][N2]   C[2]: [N0][N1][W2],  Wd = S_d * 2t
+  const int* kf[3];
+  const int* kl[3];
+  float2* C[3];
+  int Wd[3];
 };
 
 // Device-side solver state (one per plan). Every iteration kernel leaves at once
@@ -57,7 +65,7 @@ struct DevState {
 enum FirstMode { FIRST_PLAIN = 0, FIRST_ITER = 1 };
 enum LastMode { LAST_PLAIN = 0, LAST_ITER = 1, LAST_PRECOND = 2, LAST_AOUT = 3 };
 enum MidMode { MID_PROP = 0, MID_LSYM = 1, MID_FWD = 2, MID_INV = 3 };
-enum ShellMode { SHELL_CORR_X = 0, SHELL_FINAL_ITER = 1, SHELL_FINAL_PRECOND = 2, SHELL_ADD_E = 3, SHELL_SET_E = 4 };
+enum ShellMode { SHELL_UPDATE_ITER = 1, SHELL_UPDATE_PRECOND = 2, SHELL_ADD_E = 3, SHELL_SET_E = 4 };
 
 struct PassArgs {
   float2* K;            // FFT buffer
@@ -80,13 +88,22 @@ struct PassArgs {
   int subs[kMaxSplit];
 };
 
-struct ShellArgs {
+// Edge corrections E_d F of one axis into the slab C[d] (Sec. 3.1 steps 1-2, 4-5).
+struct CorrArgs {
   const float2* F;      // field the corrections are taken of
-  float2* K;            // FFT buffer
-  float2* X;            // field (updated in FINAL_ITER)
+  const float2* cW;     // c * W, t x t, row-major
+  AxisTables tb;
+  GridDesc g;
+  const DevState* state;
+  int axis;
+};
+
+// Voxels of the boundary layers: sum of the slabs, then the mode's update.
+struct ShellArgs {
+  const float2* E;      // e = x - w on the layers (UPDATE modes)
+  float2* X;            // field (updated in UPDATE_ITER)
   float2* out;          // operator output
   const float2* B;
-  const float2* cW;     // c * W, t x t, row-major
   float alpha;
   AxisTables tb;
   GridDesc g;
@@ -102,6 +119,7 @@ cudaError_t launch_strided(int n, int axis, bool inv, const PassArgs& a, cudaStr
 cudaError_t launch_mid(int n, const PassArgs& a, cudaStream_t st);
 bool fft_size_compiled(int n);
 
+cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st);
 cudaError_t launch_shell(const ShellArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_finalize(DevState* state, const double* p1, int n1, const double* p2, int n2, double* history,
                             cudaStream_t st);

@@ -18,6 +18,7 @@
 #pragma once
 #include "mbs_fft.cuh"
 #include "mbs_internal.h"
+#include "mbs_slab.cuh"
 
 namespace mbs {
 
@@ -40,55 +41,96 @@ __device__ __forceinline__ float2 (*tile_of(float2* dyn))[kPad] {
 }
 
 // ---------------------------------------------------------------------------
-// Axis-2 forward pass with the fused medium/source/correction prologue.
+// Row tiles: 32 consecutive grid rows (i0, i1) x one axis-2 subdomain segment.
+// Per-row data is set up by the first warp; the staged global traffic is
+// issued in chunks of CH independent loads per thread (memory-level
+// parallelism), then consumed.
+// ---------------------------------------------------------------------------
+struct RowInfo {
+  long long base;  // global index of element 0 of the segment
+  long long i0, i1;
+  int flags;       // bit0 valid, bit1 row inside an axis-0/1 boundary layer, bit2 row inside the source box
+  RowSlab rs;
+};
+
+__device__ __forceinline__ void setup_rows(RowInfo* ri, const PassArgs& a, int off2) {
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    const long long rows = a.g.N0 * a.g.N1;
+    const long long rho = (long long)blockIdx.x * 32 + tid;
+    RowInfo r;
+    r.flags = 0;
+    r.base = 0;
+    r.i0 = r.i1 = 0;
+    r.rs = RowSlab{-1, -1, -1, -1};
+    if (rho < rows) {
+      r.i0 = rho / a.g.N1;
+      r.i1 = rho - r.i0 * a.g.N1;
+      r.base = rho * a.g.N2 + off2;
+      r.flags = 1;
+      if (a.tb.shell[0][r.i0] | a.tb.shell[1][r.i1]) r.flags |= 2;
+      if (a.S && r.i0 >= a.sbox[0] && r.i0 < a.sbox[1] && r.i1 >= a.sbox[2] && r.i1 < a.sbox[3]) r.flags |= 4;
+      r.rs = row_slab(a.tb, r.i0, r.i1);
+    }
+    ri[tid] = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Axis-2 forward pass with the fused medium/source/correction prologue:
+// u = B x + y - E x (FIRST_ITER) or u = x (FIRST_PLAIN), then the transform.
 // ---------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(32 * warps_for(N)) k_rows_first(const __grid_constant__ PassArgs a) {
   constexpr int W = warps_for(N);
+  constexpr int NT = 32 * W;
+  constexpr int PERT = (32 * N + NT - 1) / NT;
+  constexpr int CH = PERT < 8 ? PERT : 8;
   extern __shared__ float2 dyn[];
   float2 (*sm)[kPad] = tile_of<N>(dyn);
-  __shared__ long long rbase[32];
-  __shared__ int rflag[32];
+  __shared__ RowInfo ri[32];
   if (a.state && a.state->done) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int j2 = a.subs[blockIdx.y];
   const int off2 = a.g.ax[2].off[j2];
-  const long long rows = a.g.N0 * a.g.N1;
-  if (tid < 32) {
-    const long long rho = (long long)blockIdx.x * 32 + tid;
-    int f = 0;
-    long long base = 0;
-    if (rho < rows) {
-      const long long i0 = rho / a.g.N1, i1 = rho - i0 * a.g.N1;
-      base = rho * a.g.N2 + off2;
-      f = 1;
-      if (a.tb.shell[0][i0] | a.tb.shell[1][i1]) f |= 2;
-      if (a.S && i0 >= a.sbox[0] && i0 < a.sbox[1] && i1 >= a.sbox[2] && i1 < a.sbox[3]) f |= 4;
-    }
-    rbase[tid] = base;
-    rflag[tid] = f;
-  }
+  setup_rows(ri, a, off2);
   __syncthreads();
   const bool iter = a.mode == FIRST_ITER;
-  for (int idx = tid; idx < 32 * N; idx += 32 * W) {
-    const int r = idx / N, e = idx - r * N;
-    const int f = rflag[r];
-    float2 u = make_float2(0.f, 0.f);
-    if (f & 1) {
-      const long long gi = rbase[r] + e;
-      const float2 x = a.X[gi];
-      if (iter) {
-        u = cmul(a.B[gi], x);
-        if ((f & 2) || a.tb.shell[2][off2 + e]) u = csub(u, a.K[gi]);
-        if (f & 4) {
-          const int i2 = off2 + e;
-          if (i2 >= a.sbox[4] && i2 < a.sbox[5]) u = cadd(u, cmul(a.mc, a.S[gi]));
+  const float2* __restrict__ X = a.X;
+  const float2* __restrict__ B = a.B;
+  for (int k0 = 0; k0 < PERT; k0 += CH) {
+    float2 xv[CH], bv[CH];
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+      const int idx = tid + (k0 + c) * NT;
+      xv[c] = make_float2(0.f, 0.f);
+      bv[c] = make_float2(0.f, 0.f);
+      if (idx < 32 * N) {
+        const int r = idx / N, e = idx - r * N;
+        if (ri[r].flags & 1) {
+          const long long gi = ri[r].base + e;
+          xv[c] = __ldg(X + gi);
+          if (iter) bv[c] = __ldg(B + gi);
         }
-      } else {
-        u = x;
       }
     }
-    sm[e][r] = u;
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+      const int idx = tid + (k0 + c) * NT;
+      if (idx < 32 * N) {
+        const int r = idx / N, e = idx - r * N;
+        const int f = ri[r].flags;
+        float2 u = xv[c];
+        if (iter && (f & 1)) {
+          u = cmul(bv[c], xv[c]);
+          const long long i2 = off2 + e;
+          if ((f & 2) || a.tb.shell[2][i2])
+            u = csub(u, slab_sum(a.tb, a.g, ri[r].rs, ri[r].i0, ri[r].i1, ri[r].i0 * a.g.N1 + ri[r].i1, i2));
+          if ((f & 4) && i2 >= a.sbox[4] && i2 < a.sbox[5]) u = cadd(u, cmul(a.mc, a.S[ri[r].base + e]));
+        }
+        sm[e][r] = u;
+      }
+    }
   }
   if constexpr (N > 1) {
     __syncthreads();
@@ -97,45 +139,57 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_rows_first(const __grid_c
     fft_run<N, W, false, false, 0, 1, true, true>(warp, lane, sm, a.tw, sld, sst);
   }
   __syncthreads();
-  for (int idx = tid; idx < 32 * N; idx += 32 * W) {
-    const int r = idx / N, e = idx - r * N;
-    if (rflag[r] & 1) a.K[rbase[r] + e] = sm[e][r];
+  float2* K = a.K;
+  for (int k0 = 0; k0 < PERT; k0++) {
+    const int idx = tid + k0 * NT;
+    if (idx < 32 * N) {
+      const int r = idx / N, e = idx - r * N;
+      if (ri[r].flags & 1) K[ri[r].base + e] = sm[e][r];
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Axis-2 inverse pass with the fused update epilogue.
+// Axis-2 inverse pass with the fused update epilogue (Eq. wavesim_iter):
+// e = x - w; away from the boundary layers r = B e, x <- x - alpha r and the
+// FP64 |r|^2; on the layers e is stored for the correction step.
 // ---------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(32 * warps_for(N)) k_rows_last(const __grid_constant__ PassArgs a) {
   constexpr int W = warps_for(N);
+  constexpr int NT = 32 * W;
+  constexpr int PERT = (32 * N + NT - 1) / NT;
+  constexpr int CH = PERT < 8 ? PERT : 8;
   extern __shared__ float2 dyn[];
   float2 (*sm)[kPad] = tile_of<N>(dyn);
-  __shared__ long long rbase[32];
-  __shared__ int rflag[32];
+  __shared__ RowInfo ri[32];
   __shared__ double red[32];
   if (a.state && a.state->done) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int j2 = a.subs[blockIdx.y];
   const int off2 = a.g.ax[2].off[j2];
-  const long long rows = a.g.N0 * a.g.N1;
-  if (tid < 32) {
-    const long long rho = (long long)blockIdx.x * 32 + tid;
-    int f = 0;
-    long long base = 0;
-    if (rho < rows) {
-      const long long i0 = rho / a.g.N1, i1 = rho - i0 * a.g.N1;
-      base = rho * a.g.N2 + off2;
-      f = 1;
-      if (a.tb.shell[0][i0] | a.tb.shell[1][i1]) f |= 2;
-    }
-    rbase[tid] = base;
-    rflag[tid] = f;
-  }
+  setup_rows(ri, a, off2);
   __syncthreads();
-  for (int idx = tid; idx < 32 * N; idx += 32 * W) {
-    const int r = idx / N, e = idx - r * N;
-    sm[e][r] = (rflag[r] & 1) ? a.K[rbase[r] + e] : make_float2(0.f, 0.f);
+  float2* K = a.K;
+  for (int k0 = 0; k0 < PERT; k0 += CH) {
+    float2 kv[CH];
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+      const int idx = tid + (k0 + c) * NT;
+      kv[c] = make_float2(0.f, 0.f);
+      if (idx < 32 * N) {
+        const int r = idx / N, e = idx - r * N;
+        if (ri[r].flags & 1) kv[c] = K[ri[r].base + e];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+      const int idx = tid + (k0 + c) * NT;
+      if (idx < 32 * N) {
+        const int r = idx / N, e = idx - r * N;
+        sm[e][r] = kv[c];
+      }
+    }
   }
   if constexpr (N > 1) {
     __syncthreads();
@@ -146,27 +200,49 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_rows_last(const __grid_co
   __syncthreads();
   double acc = 0.0;
   const int mode = a.mode;
-  for (int idx = tid; idx < 32 * N; idx += 32 * W) {
-    const int r = idx / N, e = idx - r * N;
-    const int f = rflag[r];
-    if (!(f & 1)) continue;
-    const long long gi = rbase[r] + e;
-    const float2 w = sm[e][r];
-    if (mode == LAST_PLAIN) {
-      a.Xout[gi] = w;
-    } else if (mode == LAST_AOUT) {
-      const float2 b = a.B[gi];
-      a.Xout[gi] = cadd(w, cmul(make_float2(1.f - b.x, -b.y), a.X[gi]));
-    } else {
-      const float2 x = a.X[gi];
-      const float2 ee = csub(x, w);
-      if ((f & 2) || a.tb.shell[2][off2 + e]) {
-        a.K[gi] = ee;  // finished by the shell kernel once all of e is known
+  const float2* X = a.X;
+  const float2* __restrict__ B = a.B;
+  const bool need_x = mode != LAST_PLAIN;
+  const bool need_b = mode != LAST_PLAIN;
+  for (int k0 = 0; k0 < PERT; k0 += CH) {
+    float2 xv[CH], bv[CH];
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+      const int idx = tid + (k0 + c) * NT;
+      xv[c] = make_float2(0.f, 0.f);
+      bv[c] = make_float2(0.f, 0.f);
+      if (idx < 32 * N) {
+        const int r = idx / N, e = idx - r * N;
+        if (ri[r].flags & 1) {
+          const long long gi = ri[r].base + e;
+          if (need_x) xv[c] = X[gi];
+          if (need_b) bv[c] = __ldg(B + gi);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+      const int idx = tid + (k0 + c) * NT;
+      if (idx >= 32 * N) continue;
+      const int r = idx / N, e = idx - r * N;
+      const int f = ri[r].flags;
+      if (!(f & 1)) continue;
+      const long long gi = ri[r].base + e;
+      const float2 w = sm[e][r];
+      if (mode == LAST_PLAIN) {
+        a.Xout[gi] = w;
+      } else if (mode == LAST_AOUT) {
+        a.Xout[gi] = cadd(w, cmul(make_float2(1.f - bv[c].x, -bv[c].y), xv[c]));
       } else {
-        const float2 rr = cmul(a.B[gi], ee);
-        acc += (double)rr.x * rr.x + (double)rr.y * rr.y;
-        a.Xout[gi] = (mode == LAST_ITER) ? make_float2(fmaf(-a.alpha, rr.x, x.x), fmaf(-a.alpha, rr.y, x.y))
-                                         : make_float2(-rr.x, -rr.y);
+        const float2 ee = csub(xv[c], w);
+        if ((f & 2) || a.tb.shell[2][off2 + e]) {
+          K[gi] = ee;  // finished by the layer update once all of e is known
+        } else {
+          const float2 rr = cmul(bv[c], ee);
+          acc += (double)rr.x * rr.x + (double)rr.y * rr.y;
+          a.Xout[gi] = (mode == LAST_ITER) ? make_float2(fmaf(-a.alpha, rr.x, xv[c].x), fmaf(-a.alpha, rr.y, xv[c].y))
+                                           : make_float2(-rr.x, -rr.y);
+        }
       }
     }
   }
@@ -208,60 +284,87 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_strided(const __grid_cons
 // ---------------------------------------------------------------------------
 // Axis-0 pass: forward transform, multiplier, inverse transform.
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(32 * warps_for(N)) k_mid(const __grid_constant__ PassArgs a) {
+struct MidPencil {
+  long long base, stride;
+  bool valid;
+  float pl;     // p1^2 + p2^2 of this pencil
+  float sc;     // 1 / (n0 n1 n2)
+  const float* p20;
+};
+
+__device__ __forceinline__ MidPencil mid_pencil(const PassArgs& a) {
+  MidPencil m;
+  const int lane = threadIdx.x & 31;
+  const int j = a.subs[blockIdx.z];
+  const int off0 = a.g.ax[0].off[j];
+  const long long i1 = blockIdx.y;
+  const long long i2 = (long long)blockIdx.x * 32 + lane;
+  m.valid = i2 < a.g.N2;
+  const long long i2c = m.valid ? i2 : 0;
+  m.base = (long long)off0 * a.g.N1 * a.g.N2 + i1 * a.g.N2 + i2;
+  m.stride = a.g.N1 * a.g.N2;
+  m.pl = a.tb.p2[1][i1] + a.tb.p2[2][i2c];
+  m.sc = a.tb.invn[0][off0] * a.tb.invn[1][i1] * a.tb.invn[2][i2c];
+  m.p20 = a.tb.p2[0] + off0;
+  return m;
+}
+
+// Propagator (L + I)^-1 = 1/(c(k0^2 - |p|^2) + 1) (Sec. 2) or the symbol of L,
+// c(k0^2 - |p|^2) (Eq. L-convolution), times 1/(n0 n1 n2).
+template <int N, int MIN_BLOCKS>
+__global__ void __launch_bounds__(32 * warps_for(N), MIN_BLOCKS) k_mid_turn(const __grid_constant__ PassArgs a) {
   constexpr int W = warps_for(N);
   extern __shared__ float2 dyn[];
   float2 (*sm)[kPad] = tile_of<N>(dyn);
   if (a.state && a.state->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j = a.subs[blockIdx.z];
-  const int off0 = a.g.ax[0].off[j];
-  const long long i1 = blockIdx.y;
-  const long long i2 = (long long)blockIdx.x * 32 + lane;
-  const bool valid = i2 < a.g.N2;
-  const long long i2c = valid ? i2 : 0;
-  const long long base = (long long)off0 * a.g.N1 * a.g.N2 + i1 * a.g.N2 + i2;
-  const long long stride = a.g.N1 * a.g.N2;
-  const float pl = a.tb.p2[1][i1] + a.tb.p2[2][i2c];
-  const float sc = a.tb.invn[0][off0] * a.tb.invn[1][i1] * a.tb.invn[2][i2c];
-  const float* p20 = a.tb.p2[0] + off0;
+  const MidPencil m = mid_pencil(a);
   const float2 c = a.c, ck0 = a.ck0;
   float2* K = a.K;
-  auto gld = [&](int e) { return valid ? K[base + e * stride] : make_float2(0.f, 0.f); };
+  auto gld = [&](int e) { return m.valid ? K[m.base + e * m.stride] : make_float2(0.f, 0.f); };
   auto gst = [&](int e, float2 v) {
-    if (valid) K[base + e * stride] = v;
+    if (m.valid) K[m.base + e * m.stride] = v;
   };
-  const int mode = a.mode;
-  auto mul_prop = [&](int e, float2 v) {
-    const float p2 = __ldg(p20 + e) + pl;
-    // den = c (k0^2 - |p|^2) + 1
-    const float dx = fmaf(-c.x, p2, ck0.x + 1.f), dy = fmaf(-c.y, p2, ck0.y);
-    const float inv = sc / fmaf(dx, dx, dy * dy);
-    return cmul(v, make_float2(dx * inv, -dy * inv));
-  };
-  auto mul_lsym = [&](int e, float2 v) {
-    const float p2 = __ldg(p20 + e) + pl;
-    return cmul(v, make_float2(fmaf(-c.x, p2, ck0.x) * sc, fmaf(-c.y, p2, ck0.y) * sc));
+  const bool prop = a.mode == MID_PROP;
+  auto mul = [&](int e, float2 v) {
+    const float p2 = __ldg(m.p20 + e) + m.pl;
+    const float dx = fmaf(-c.x, p2, ck0.x), dy = fmaf(-c.y, p2, ck0.y);  // c (k0^2 - |p|^2)
+    if (prop) {
+      const float ex = dx + 1.f;
+      const float inv = m.sc / fmaf(ex, ex, dy * dy);
+      return cmul(v, make_float2(ex * inv, -dy * inv));
+    }
+    return cmul(v, make_float2(dx * m.sc, dy * m.sc));
   };
   if constexpr (N == 1) {
-    if (valid) {
-      float2 v = K[base];
-      if (mode == MID_PROP) v = mul_prop(0, v);
-      else if (mode == MID_LSYM) v = mul_lsym(0, v);
-      else if (mode == MID_INV) v = cscale(v, sc);
-      K[base] = v;
-    }
+    if (m.valid) K[m.base] = mul(0, K[m.base]);
   } else {
-    if (mode == MID_PROP) {
-      fft_fwd_mul_inv<N, W, false, false>(warp, lane, sm, a.tw, gld, gst, mul_prop);
-    } else if (mode == MID_LSYM) {
-      fft_fwd_mul_inv<N, W, false, false>(warp, lane, sm, a.tw, gld, gst, mul_lsym);
-    } else if (mode == MID_FWD) {
-      fft_run<N, W, false, false, 0, 1, false, false>(warp, lane, sm, a.tw, gld, gst);
-    } else {
-      auto gls = [&](int e) { return cscale(gld(e), sc); };
+    fft_fwd_mul_inv<N, W, false, false>(warp, lane, sm, a.tw, gld, gst, mul);
+  }
+}
+
+// Forward-only (MID_FWD) or scaled inverse-only (MID_INV) axis-0 transform.
+template <int N>
+__global__ void __launch_bounds__(32 * warps_for(N)) k_mid_plain(const __grid_constant__ PassArgs a) {
+  constexpr int W = warps_for(N);
+  extern __shared__ float2 dyn[];
+  float2 (*sm)[kPad] = tile_of<N>(dyn);
+  if (a.state && a.state->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const MidPencil m = mid_pencil(a);
+  float2* K = a.K;
+  auto gst = [&](int e, float2 v) {
+    if (m.valid) K[m.base + e * m.stride] = v;
+  };
+  if (a.mode == MID_FWD) {
+    auto gld = [&](int e) { return m.valid ? K[m.base + e * m.stride] : make_float2(0.f, 0.f); };
+    if constexpr (N > 1) fft_run<N, W, false, false, 0, 1, false, false>(warp, lane, sm, a.tw, gld, gst);
+  } else {
+    auto gls = [&](int e) { return m.valid ? cscale(K[m.base + e * m.stride], m.sc) : make_float2(0.f, 0.f); };
+    if constexpr (N > 1) {
       fft_run<N, W, true, false, 0, 1, false, false>(warp, lane, sm, a.tw, gls, gst);
+    } else {
+      if (m.valid) K[m.base] = gls(0);
     }
   }
 }
@@ -270,6 +373,9 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_mid(const __grid_constant
 // Launch helpers for one size.
 // ---------------------------------------------------------------------------
 inline size_t tile_bytes(int n) { return (size_t)n * kPad * sizeof(float2); }
+
+// Resident CTAs per SM asked of the register allocator for the axis-0 pass.
+constexpr int mid_min_blocks(int n) { return n >= 64 && n <= 256 ? 3 : 1; }
 
 // Opt in to more than 48 KB of dynamic shared memory once per kernel.
 template <class K>
@@ -325,9 +431,16 @@ cudaError_t run_size(int kind, int axis, bool inv, const PassArgs& a, int nrow_b
       break;
     }
     case 3: {
-      e = set_smem(k_mid<N>, sm);
-      if (e) return e;
-      k_mid<N><<<dim3(gx, (unsigned)a.g.N1, a.nsub), blk, sm, st>>>(a);
+      const dim3 grd(gx, (unsigned)a.g.N1, a.nsub);
+      if (a.mode == MID_PROP || a.mode == MID_LSYM) {
+        e = set_smem(k_mid_turn<N, mid_min_blocks(N)>, sm);
+        if (e) return e;
+        k_mid_turn<N, mid_min_blocks(N)><<<grd, blk, sm, st>>>(a);
+      } else {
+        e = set_smem(k_mid_plain<N>, sm);
+        if (e) return e;
+        k_mid_plain<N><<<grd, blk, sm, st>>>(a);
+      }
       break;
     }
     default:
