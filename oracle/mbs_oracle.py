@@ -25,7 +25,9 @@ Readings where the paper is silent (each is also listed in the design notes):
   R6  Stop after the update in which eps_n < tol (strict).
   R8  Absorbing layers lie inside the grid: on each non-zero face width w the
       imaginary part of the index ramps linearly, adding kappa*(w - i)/w at
-      depth i = 0..w-1 from the face; contributions of different faces add.
+      depth i = 0..w-1 from the face; where faces meet the largest ramp applies
+      (so corners do not raise ||k^2 - k0^2||_inf and with it the iteration
+      count, Eq. c_scale).
   R9  A periodic, split axis transfers across the global seam (a_d = 2).
   R14 If the denominator of Eq. c_scale2 is zero, it is replaced by 0.05*max|k^2|.
 Parity unpinned: none of the functions below (all are pinned by the tests).
@@ -164,20 +166,25 @@ def split_sizes(total: int, parts: int, explicit=None):
 
 
 def absorbing_index(n: np.ndarray, widths, kappa: float) -> np.ndarray:
-    """Refractive index with linear imaginary ramps on the boundary faces (reading R8)."""
+    """Refractive index with linear imaginary ramps on the boundary faces (reading R8).
+
+    On a face of width w the ramp is (w - i)/w at depth i = 0..w-1 from the face;
+    where layers of several faces meet, the largest ramp applies.
+    """
     out = np.array(n, dtype=np.complex128)
+    ramp3 = np.zeros(out.shape)
     for d in range(3):
         size = out.shape[d]
         ramp = np.zeros(size)
         lo, hi = widths[d]
         for i in range(min(lo, size)):
-            ramp[i] += (lo - i) / lo
+            ramp[i] = max(ramp[i], (lo - i) / lo)
         for i in range(min(hi, size)):
-            ramp[size - 1 - i] += (hi - i) / hi
+            ramp[size - 1 - i] = max(ramp[size - 1 - i], (hi - i) / hi)
         shape = [1, 1, 1]
         shape[d] = size
-        out = out + 1j * kappa * ramp.reshape(shape)
-    return out
+        ramp3 = np.maximum(ramp3, ramp.reshape(shape))
+    return out + 1j * kappa * ramp3
 
 
 def axis_flags(split, periodic):
