@@ -104,7 +104,8 @@ MBS_API void mbs_default_options(mbs_options *opts);
  * refractive index `refractive_index` (complex64, shape; host or device), and
  * absorbing layers of boundary_widths[2d], boundary_widths[2d+1] pixels on the
  * low and high face of axis d (added inside the grid as a linear ramp of the
- * imaginary index). `split` gives the subdomains per axis (Sec. 3: any number
+ * imaginary index, absorb_kappa * (w - i)/w at depth i from a face of width w;
+ * where faces meet the largest ramp applies). `split` gives the subdomains per axis (Sec. 3: any number
  * along any axis, unequal sizes allowed). The plan computes, in FP64 on the
  * device: k^2, k0^2 (centre of the bounding box of k^2 in C), the scale c of
  * Eq. c_scale2 with ||A12|| the spectral norm of the t x t block W, and the

@@ -127,9 +127,8 @@ struct mbs_plan {
   float2* tmp_in;
   float2* tmp_out;
   float *p2[3], *invn[3];
-  int *sub[3], *loc[3], *sh2list, *kf[3], *kl[3];
-  float2* slab[3];
-  int Wd[3];
+  int *sub[3], *loc[3], *sh2list;
+  float2* ebuf;  // e = x - w on the boundary layers
   unsigned char* shell[3];
   int nsh2;
   float2* cW;
@@ -187,19 +186,15 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
   char* pB = take(F);
   char* pK = take(F);
   char* psrc = take(F);
-  char *pp2[3], *pinv[3], *psub[3], *ploc[3], *psh[3], *pkf[3], *pkl[3], *pslab[3];
+  const bool corr = p->t > 0 && (p->a[0] > 0 || p->a[1] > 0 || p->a[2] > 0);
+  char* pe = corr ? take(F) : nullptr;
+  char *pp2[3], *pinv[3], *psub[3], *ploc[3], *psh[3];
   for (int d = 0; d < 3; d++) {
     pp2[d] = take(p->N[d] * sizeof(float));
     pinv[d] = take(p->N[d] * sizeof(float));
     psub[d] = take(p->N[d] * sizeof(int));
     ploc[d] = take(p->N[d] * sizeof(int));
     psh[d] = take(p->N[d]);
-    pkf[d] = take(p->N[d] * sizeof(int));
-    pkl[d] = take(p->N[d] * sizeof(int));
-    // correction slab of axis d: S_d * 2t layers times the two other extents
-    const int64_t other = nvox(p) / p->N[d];
-    const bool corr = p->t > 0 && p->a[d] > 0;
-    pslab[d] = corr ? take((size_t)p->S[d] * 2 * p->t * other * sizeof(float2)) : nullptr;
   }
   char* psh2 = take(p->N[2] * sizeof(int));
   char* pcw = take(std::max(1, p->t * p->t) * sizeof(float2));
@@ -227,11 +222,8 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
       p->sub[d] = (int*)psub[d];
       p->loc[d] = (int*)ploc[d];
       p->shell[d] = (unsigned char*)psh[d];
-      p->kf[d] = (int*)pkf[d];
-      p->kl[d] = (int*)pkl[d];
-      p->slab[d] = (float2*)pslab[d];
-      p->Wd[d] = p->S[d] * 2 * p->t;
     }
+    p->ebuf = (float2*)pe;
     p->sh2list = (int*)psh2;
     p->cW = (float2*)pcw;
     p->tw.clear();
@@ -339,7 +331,6 @@ mbs_status upload_tables(mbs_plan* p) {
     std::vector<float> p2(N), invn(N);
     std::vector<int> sub(N), loc(N);
     std::vector<unsigned char> sh(N);
-    std::vector<int> kf(N, -1), kl(N, -1);
     const int t = p->t;
     for (int s = 0; s < p->S[d]; s++) {
       const int n = p->sizes[d][s], o = p->offs[d][s];
@@ -352,12 +343,9 @@ mbs_status upload_tables(mbs_plan* p) {
         loc[o + q] = q;
         const bool corr = t > 0 && p->a[d] > 0;
         sh[o + q] = (corr && (q < t || q >= n - t)) ? 1 : 0;
-        if (corr && q < t) kf[o + q] = s * 2 * t + q;
-        if (corr && q >= n - t) kl[o + q] = s * 2 * t + t + (q - (n - t));
       }
     }
-    CU(cudaMemcpyAsync(p->kf[d], kf.data(), N * sizeof(int), cudaMemcpyHostToDevice, p->stream));
-    CU(cudaMemcpyAsync(p->kl[d], kl.data(), N * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+
     CU(cudaMemcpyAsync(p->p2[d], p2.data(), N * sizeof(float), cudaMemcpyHostToDevice, p->stream));
     CU(cudaMemcpyAsync(p->invn[d], invn.data(), N * sizeof(float), cudaMemcpyHostToDevice, p->stream));
     CU(cudaMemcpyAsync(p->sub[d], sub.data(), N * sizeof(int), cudaMemcpyHostToDevice, p->stream));
@@ -391,10 +379,6 @@ mbs_status upload_tables(mbs_plan* p) {
     tb.sub[d] = p->sub[d];
     tb.loc[d] = p->loc[d];
     tb.shell[d] = p->shell[d];
-    tb.kf[d] = p->kf[d];
-    tb.kl[d] = p->kl[d];
-    tb.C[d] = p->slab[d];
-    tb.Wd[d] = p->Wd[d];
   }
   tb.sh2list = p->sh2list;
   tb.nsh2 = p->nsh2;
@@ -450,6 +434,7 @@ PassArgs base_args(mbs_plan* p) {
   PassArgs a;
   memset(&a, 0, sizeof(a));
   a.K = p->K;
+  a.E = p->ebuf;
   a.B = p->B;
   a.c = make_float2((float)p->c_re, (float)p->c_im);
   const double ck0r = p->c_re * p->k0_re - p->c_im * p->k0_im;
@@ -465,7 +450,8 @@ PassArgs base_args(mbs_plan* p) {
 ShellArgs shell_args(mbs_plan* p) {
   ShellArgs s;
   memset(&s, 0, sizeof(s));
-  s.E = p->K;
+  s.E = p->ebuf;
+  s.C = p->K;
   s.X = p->x;
   s.B = p->B;
   s.alpha = (float)p->alpha;
@@ -474,8 +460,8 @@ ShellArgs shell_args(mbs_plan* p) {
   return s;
 }
 
-// Edge corrections of field F along every corrected axis into the slabs.
-cudaError_t run_corr(mbs_plan* p, const float2* F, const DevState* state);
+// Edge corrections E F into the buffer C at the boundary-layer voxels.
+cudaError_t run_corr(mbs_plan* p, const float2* F, float2* C, const DevState* state);
 
 int nrow_blocks(const mbs_plan* p) { return (int)((p->N[0] * p->N[1] + 31) / 32); }
 
@@ -502,10 +488,11 @@ struct Recorder {
   }
 };
 
-cudaError_t run_corr_rec(mbs_plan* p, const float2* F, const DevState* state, Recorder* rec, int kind) {
+cudaError_t run_corr_rec(mbs_plan* p, const float2* F, float2* C, const DevState* state, Recorder* rec, int kind) {
   CorrArgs c;
   memset(&c, 0, sizeof(c));
   c.F = F;
+  c.C = C;
   c.cW = p->cW;
   c.tb = p->tb;
   c.g = p->g;
@@ -521,8 +508,8 @@ cudaError_t run_corr_rec(mbs_plan* p, const float2* F, const DevState* state, Re
   return cudaSuccess;
 }
 
-cudaError_t run_corr(mbs_plan* p, const float2* F, const DevState* state) {
-  return run_corr_rec(p, F, state, nullptr, 0);
+cudaError_t run_corr(mbs_plan* p, const float2* F, float2* C, const DevState* state) {
+  return run_corr_rec(p, F, C, state, nullptr, 0);
 }
 
 // The forward half shared by the iteration and several operators:
@@ -603,8 +590,8 @@ cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
     a.S = p->src;
     for (int i = 0; i < 6; i++) a.sbox[i] = p->sbox[i];
   }
-  if (p->has_shell) {  // V #1: E x into the slabs (steps 1-2)
-    e = run_corr_rec(p, p->x, p->state, rec, KK_CORR_X);
+  if (p->has_shell) {  // V #1: E x on the boundary layers, into the FFT buffer (steps 1-2)
+    e = run_corr_rec(p, p->x, p->K, p->state, rec, KK_CORR_X);
     if (e) return e;
   }
   e = run_transform_chain(p, a, FIRST_ITER, MID_PROP, rec);
@@ -612,8 +599,8 @@ cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
   e = run_rows_last(p, a, LAST_ITER, true, rec);
   if (e) return e;
   double* pshell = p->partials + p->n_rows_partials;
-  if (p->has_shell) {  // V #2 on e = x - w: E e, then the layer voxels' update
-    e = run_corr_rec(p, p->K, p->state, rec, KK_CORR_E);
+  if (p->has_shell) {  // V #2 on e = x - w: E e into the (now free) FFT buffer, then the layers' update
+    e = run_corr_rec(p, p->ebuf, p->K, p->state, rec, KK_CORR_E);
     if (e) return e;
     ShellArgs s = shell_args(p);
     s.state = p->state;
@@ -835,7 +822,7 @@ mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* o
       e = run_transform_chain(p, a, FIRST_PLAIN, MID_LSYM, nullptr);
       if (!e) e = run_rows_last(p, a, LAST_AOUT, false, nullptr);
       if (!e && p->has_shell) {
-        e = run_corr(p, xd, p->free_state);
+        e = run_corr(p, xd, p->K, p->free_state);
         s.mode = SHELL_ADD_E;
         if (!e) e = launch_shell(s, kShellBlocks, p->stream);
       }
@@ -845,11 +832,11 @@ mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* o
         a.S = p->src;
         for (int i = 0; i < 6; i++) a.sbox[i] = p->sbox[i];
       }
-      if (p->has_shell) e = run_corr(p, xd, p->free_state);
+      if (p->has_shell) e = run_corr(p, xd, p->K, p->free_state);
       if (!e) e = run_transform_chain(p, a, FIRST_ITER, MID_PROP, nullptr);
       if (!e) e = run_rows_last(p, a, LAST_PRECOND, false, nullptr);
       if (!e && p->has_shell) {
-        e = run_corr(p, p->K, p->free_state);
+        e = run_corr(p, p->ebuf, p->K, p->free_state);
         s.mode = SHELL_UPDATE_PRECOND;
         if (!e) e = launch_shell(s, kShellBlocks, p->stream);
       }
@@ -857,7 +844,7 @@ mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* o
     case MBS_OP_V:
       e = launch_pointwise_V(xd, p->B, od, nv, p->stream);
       if (!e && p->has_shell) {
-        e = run_corr(p, xd, p->free_state);
+        e = run_corr(p, xd, p->K, p->free_state);
         s.mode = SHELL_ADD_E;
         if (!e) e = launch_shell(s, kShellBlocks, p->stream);
       }
@@ -865,7 +852,7 @@ mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* o
     case MBS_OP_E:
       e = launch_zero(od, nv, p->stream);
       if (!e && p->has_shell) {
-        e = run_corr(p, xd, p->free_state);
+        e = run_corr(p, xd, p->K, p->free_state);
         s.mode = SHELL_SET_E;
         if (!e) e = launch_shell(s, kShellBlocks, p->stream);
       }

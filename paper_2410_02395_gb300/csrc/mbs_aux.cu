@@ -3,7 +3,6 @@
 
 #include "mbs_fft.cuh"
 #include "mbs_internal.h"
-#include "mbs_slab.cuh"
 #include "../../include/mbs.h"
 
 namespace mbs {
@@ -16,33 +15,38 @@ namespace mbs {
 //   last t layers  (row a of W):   (E f)_s[n-t+a] = sum_b cW[a][b] (f_right[b]      - f_s[b])
 //   first t layers (row a of W^T): (E f)_s[a]     = sum_b cW[b][a] (f_left[n_l-t+b] - f_s[n-t+b])
 // A missing neighbour contributes nothing (wrap removal only, step 4); a present
-// one adds its transfer (step 5). One thread per (pencil, subdomain) loads the
-// 4t inputs once, keeps the differences in registers and writes the 2t outputs
-// into the axis's slab; the terms of different axes are added by the consumers.
+// one adds its transfer (step 5). If n < 2t a voxel can be in both ranges and
+// gets both terms. The terms of different axes add: axes run in order 0, 1, 2
+// and a launch adds to the buffer where an earlier axis already wrote.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void put(float2* C, long long v, float2 val, bool add) {
+  C[v] = add ? cadd(C[v], val) : val;
+}
+
+// Axes 0 and 1: one thread per (pencil, subdomain); consecutive threads take
+// consecutive axis-2 positions, so every load and store is coalesced.
 template <int TM>
-__global__ void __launch_bounds__(128) k_corr(const __grid_constant__ CorrArgs a) {
+__global__ void __launch_bounds__(128) k_corr_strided(const __grid_constant__ CorrArgs a) {
   if (a.state && a.state->done) return;
   const int d = a.axis;
   const AxisDesc& ax = a.g.ax[d];
   const long long N0 = a.g.N0, N1 = a.g.N1, N2 = a.g.N2;
-  const int t = a.g.t, Wd = a.tb.Wd[d];
-  const long long npen = d == 0 ? N1 * N2 : (d == 1 ? N0 * N2 : N0 * N1);
+  const int t = a.g.t;
+  const long long npen = d == 0 ? N1 * N2 : N0 * N2;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= npen * ax.S) return;
   const int s = (int)(gid / npen);
   const long long p = gid - (long long)s * npen;
   long long base, stride;
+  bool add = false;
   if (d == 0) {
     base = p;
     stride = N1 * N2;
-  } else if (d == 1) {
+  } else {
     const long long i0 = p / N2, i2 = p - i0 * N2;
     base = i0 * N1 * N2 + i2;
     stride = N2;
-  } else {
-    base = p * N2;
-    stride = 1;
+    add = a.tb.shell[0][i0];
   }
   const int off = ax.off[s], n = ax.n[s];
   const int L = ax.left[s], R = ax.right[s];
@@ -61,49 +65,111 @@ __global__ void __launch_bounds__(128) k_corr(const __grid_constant__ CorrArgs a
       D[b] = E[b] = make_float2(0.f, 0.f);
     }
   }
-  float2* C = a.tb.C[d];
   const float2* __restrict__ cW = a.cW;
+  auto last_val = [&](int aa) {
+    float2 v = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int aa = 0; aa < TM; aa++) {
-    if (aa < t) {
-      float2 af = make_float2(0.f, 0.f), al = make_float2(0.f, 0.f);
+    for (int b = 0; b < TM; b++)
+      if (b < t) v = cadd(v, cmul(__ldg(cW + aa * t + b), D[b]));
+    return v;
+  };
+  float2* C = a.C;
 #pragma unroll
-      for (int b = 0; b < TM; b++) {
-        if (b < t) {
-          af = cadd(af, cmul(__ldg(cW + b * t + aa), E[b]));
-          al = cadd(al, cmul(__ldg(cW + aa * t + b), D[b]));
+  for (int q = 0; q < TM; q++) {  // first t layers (q < t), plus the last-range term if they overlap
+    if (q < t) {
+      float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < TM; b++)
+        if (b < t) v = cadd(v, cmul(__ldg(cW + b * t + q), E[b]));
+      if (q >= n - t) v = cadd(v, last_val(q - (n - t)));
+      put(C, base + (long long)(off + q) * stride, v, add);
+    }
+  }
+#pragma unroll
+  for (int aa = 0; aa < TM; aa++) {  // last t layers not already written above
+    const int q = n - t + aa;
+    if (aa < t && q >= t) put(C, base + (long long)(off + q) * stride, last_val(aa), add);
+  }
+}
+
+// Axis 2: one warp per grid row; the row's 2t layer values of every subdomain
+// are staged in shared memory with coalesced loads, then each lane produces
+// outputs from shared memory.
+__global__ void __launch_bounds__(256) k_corr_rows(const __grid_constant__ CorrArgs a) {
+  extern __shared__ float2 cs[];
+  if (a.state && a.state->done) return;
+  const AxisDesc& ax = a.g.ax[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = a.g.t, S = ax.S, M = S * 2 * t;
+  float2* sm = cs + warp * M;
+  const long long N1 = a.g.N1, N2 = a.g.N2, rows = a.g.N0 * N1;
+  const float2* __restrict__ F = a.F;
+  const float2* __restrict__ cW = a.cW;
+  float2* C = a.C;
+  for (long long rho = (long long)blockIdx.x * 8 + warp; rho < rows; rho += (long long)gridDim.x * 8) {
+    const long long i0 = rho / N1, i1 = rho - i0 * N1;
+    const bool add = a.tb.shell[0][i0] || a.tb.shell[1][i1];
+    const long long rb = rho * N2;
+    for (int idx = lane; idx < M; idx += 32) {
+      const int s = idx / (2 * t), k = idx - s * 2 * t;
+      const int q = k < t ? k : ax.n[s] - t + (k - t);
+      sm[idx] = F[rb + ax.off[s] + q];
+    }
+    __syncwarp();
+    for (int idx = lane; idx < M; idx += 32) {
+      const int s = idx / (2 * t), k = idx - s * 2 * t;
+      const int n = ax.n[s];
+      const float2* own = sm + s * 2 * t;  // own[0..t): first t layers, own[t..2t): last t layers
+      const float2* lf = ax.left[s] >= 0 ? sm + ax.left[s] * 2 * t + t : nullptr;
+      const float2* rf = ax.right[s] >= 0 ? sm + ax.right[s] * 2 * t : nullptr;
+      // local position q of this output; in the last range, voxels that are also
+      // in the first range (n < 2t) are produced by the first-range lane
+      const int q = k < t ? k : n - t + (k - t);
+      if (k >= t && q < t) continue;
+      float2 v = make_float2(0.f, 0.f);
+      if (q < t) {  // first t layers: row q of W^T on (left's last t - own last t)
+        for (int b = 0; b < t; b++) {
+          const float2 f = lf ? csub(lf[b], own[t + b]) : make_float2(-own[t + b].x, -own[t + b].y);
+          v = cadd(v, cmul(__ldg(cW + b * t + q), f));
         }
       }
-      const int kf = s * 2 * t + aa, kl = s * 2 * t + t + aa;
-      if (d == 0) {
-        C[(long long)kf * N1 * N2 + p] = af;
-        C[(long long)kl * N1 * N2 + p] = al;
-      } else if (d == 1) {
-        const long long i0 = p / N2, i2 = p - i0 * N2;
-        C[(i0 * Wd + kf) * N2 + i2] = af;
-        C[(i0 * Wd + kl) * N2 + i2] = al;
-      } else {
-        C[p * Wd + kf] = af;
-        C[p * Wd + kl] = al;
+      if (q >= n - t) {  // last t layers: row q-(n-t) of W on (right's first t - own first t)
+        const int aa = q - (n - t);
+        for (int b = 0; b < t; b++) {
+          const float2 f = rf ? csub(rf[b], own[b]) : make_float2(-own[b].x, -own[b].y);
+          v = cadd(v, cmul(__ldg(cW + aa * t + b), f));
+        }
       }
+      put(C, rb + ax.off[s] + q, v, add);
     }
+    __syncwarp();
   }
 }
 
 cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st) {
   const AxisDesc& ax = a.g.ax[a.axis];
-  const long long npen = a.axis == 0 ? a.g.N1 * a.g.N2 : (a.axis == 1 ? a.g.N0 * a.g.N2 : a.g.N0 * a.g.N1);
-  const long long nth = npen * ax.S;
-  const unsigned blocks = (unsigned)((nth + 127) / 128);
   const int t = a.g.t;
+  if (a.axis == 2) {
+    const size_t smem = (size_t)8 * ax.S * 2 * t * sizeof(float2);
+    if (smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(k_corr_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e) return e;
+    }
+    const long long rows = a.g.N0 * a.g.N1;
+    const long long blocks = (rows + 7) / 8 < 152 * 16 ? (rows + 7) / 8 : 152 * 16;
+    k_corr_rows<<<(unsigned)blocks, 256, smem, st>>>(a);
+    return cudaGetLastError();
+  }
+  const long long npen = a.axis == 0 ? a.g.N1 * a.g.N2 : a.g.N0 * a.g.N2;
+  const unsigned blocks = (unsigned)((npen * ax.S + 127) / 128);
   if (t <= 4)
-    k_corr<4><<<blocks, 128, 0, st>>>(a);
+    k_corr_strided<4><<<blocks, 128, 0, st>>>(a);
   else if (t <= 8)
-    k_corr<8><<<blocks, 128, 0, st>>>(a);
+    k_corr_strided<8><<<blocks, 128, 0, st>>>(a);
   else if (t <= 16)
-    k_corr<16><<<blocks, 128, 0, st>>>(a);
+    k_corr_strided<16><<<blocks, 128, 0, st>>>(a);
   else
-    k_corr<32><<<blocks, 128, 0, st>>>(a);
+    k_corr_strided<32><<<blocks, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -121,46 +187,60 @@ __device__ __forceinline__ double block_sum_all(double v, double* red) {
 
 // Boundary-layer voxels: one warp per grid row (i0, i1); a row inside an
 // axis-0/1 layer is processed whole, other rows only at the axis-2 layers.
-// E = sum of the slabs at the voxel, then per mode:
+// With E = C[v] (the summed corrections of the voxel), per mode:
 //   UPDATE_ITER:    r = B e - E, x <- x - alpha r, FP64 |r|^2   (e from the last pass)
 //   UPDATE_PRECOND: out = -(B e - E)
 //   ADD_E:          out += E          SET_E: out = E
+// Each lane handles up to 8 voxels of a row per round with all loads issued first.
 __global__ void __launch_bounds__(256) k_shell(const __grid_constant__ ShellArgs a) {
   __shared__ double red[8];
   if (a.state && a.state->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long N1 = a.g.N1, N2 = a.g.N2;
   const long long rows = a.g.N0 * N1;
+  const int mode = a.mode;
+  const bool upd = mode == SHELL_UPDATE_ITER || mode == SHELL_UPDATE_PRECOND;
+  constexpr int U = 8;
   double acc = 0.0;
   for (long long rho = (long long)blockIdx.x * 8 + warp; rho < rows; rho += (long long)gridDim.x * 8) {
     const long long i0 = rho / N1, i1 = rho - i0 * N1;
     const bool full = a.tb.shell[0][i0] || a.tb.shell[1][i1];
     const long long cnt = full ? N2 : a.tb.nsh2;
-    if (cnt == 0) continue;
-    const RowSlab rs = row_slab(a.tb, i0, i1);
-    for (long long k = lane; k < cnt; k += 32) {
-      const long long i2 = full ? k : a.tb.sh2list[k];
-      const long long v = rho * N2 + i2;
-      const float2 E = slab_sum(a.tb, a.g, rs, i0, i1, rho, i2);
-      switch (a.mode) {
-        case SHELL_UPDATE_ITER:
-        case SHELL_UPDATE_PRECOND: {
-          const float2 r = csub(cmul(a.B[v], a.E[v]), E);
-          acc += (double)r.x * r.x + (double)r.y * r.y;
-          if (a.mode == SHELL_UPDATE_ITER) {
-            const float2 x = a.X[v];
-            a.X[v] = make_float2(fmaf(-a.alpha, r.x, x.x), fmaf(-a.alpha, r.y, x.y));
-          } else {
-            a.out[v] = make_float2(-r.x, -r.y);
+    for (long long k0 = 0; k0 < cnt; k0 += 32 * U) {
+      long long v[U];
+      float2 ev[U], cv[U], xv[U], bv[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const long long k = k0 + lane + 32 * u;
+        v[u] = -1;
+        if (k < cnt) {
+          const long long i2 = full ? k : a.tb.sh2list[k];
+          v[u] = rho * N2 + i2;
+          cv[u] = a.C[v[u]];
+          if (upd) {
+            ev[u] = a.E[v[u]];
+            bv[u] = a.B[v[u]];
+            if (mode == SHELL_UPDATE_ITER) xv[u] = a.X[v[u]];
+          } else if (mode == SHELL_ADD_E) {
+            xv[u] = a.out[v[u]];
           }
-          break;
         }
-        case SHELL_ADD_E:
-          a.out[v] = cadd(a.out[v], E);
-          break;
-        default:
-          a.out[v] = E;
-          break;
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (v[u] < 0) continue;
+        if (upd) {
+          const float2 r = csub(cmul(bv[u], ev[u]), cv[u]);
+          acc += (double)r.x * r.x + (double)r.y * r.y;
+          if (mode == SHELL_UPDATE_ITER)
+            a.X[v[u]] = make_float2(fmaf(-a.alpha, r.x, xv[u].x), fmaf(-a.alpha, r.y, xv[u].y));
+          else
+            a.out[v[u]] = make_float2(-r.x, -r.y);
+        } else if (mode == SHELL_ADD_E) {
+          a.out[v[u]] = cadd(xv[u], cv[u]);
+        } else {
+          a.out[v[u]] = cv[u];
+        }
       }
     }
   }
@@ -243,12 +323,15 @@ cudaError_t launch_state_arm(DevState* state, int add_iter, double tol, int rese
 // ---------------------------------------------------------------------------
 // Plan set-up in FP64: absorbing ramp, k^2, bounds, contrast and B.
 // ---------------------------------------------------------------------------
+// Linear absorbing ramp of one axis: (w - i)/w at depth i from a face of width
+// w, the larger of the two faces' values; the voxel's ramp is the largest over
+// the three axes (faces meeting at edges and corners do not add).
 struct Ramp {
   __device__ static double at(long long i, long long N, int lo, int hi) {
     double r = 0.0;
-    if (lo > 0 && i < lo) r += (double)(lo - i) / lo;
+    if (lo > 0 && i < lo) r = fmax(r, (double)(lo - i) / lo);
     const long long j = N - 1 - i;
-    if (hi > 0 && j < hi) r += (double)(hi - j) / hi;
+    if (hi > 0 && j < hi) r = fmax(r, (double)(hi - j) / hi);
     return r;
   }
 };
@@ -256,7 +339,8 @@ struct Ramp {
 __device__ __forceinline__ void k2_at(const float2* n, long long v, const GridDesc& g, const int* w, double kappa,
                                       double lambda, double& kr, double& ki) {
   const long long i0 = v / (g.N1 * g.N2), rem = v - i0 * g.N1 * g.N2, i1 = rem / g.N2, i2 = rem - i1 * g.N2;
-  const double ramp = Ramp::at(i0, g.N0, w[0], w[1]) + Ramp::at(i1, g.N1, w[2], w[3]) + Ramp::at(i2, g.N2, w[4], w[5]);
+  const double ramp = fmax(fmax(Ramp::at(i0, g.N0, w[0], w[1]), Ramp::at(i1, g.N1, w[2], w[3])),
+                           Ramp::at(i2, g.N2, w[4], w[5]));
   const float2 nn = n[v];
   const double nr = nn.x, ni = (double)nn.y + kappa * ramp;
   const double s = 2.0 * 3.14159265358979323846 / lambda;

@@ -37,14 +37,6 @@ struct AxisTables {
   const unsigned char* shell[3];  // 1 if a_d >= 1 and the voxel lies in the first/last t layers
   const int* sh2list;     // global axis-2 indices with shell[2] set
   int nsh2;
-  // Edge-correction slabs: for axis d the corrections of the first t and last t
-  // layers of every subdomain, slab row k = s*2t + a (first t) or s*2t + t + a
-  // (last t). kf/kl give that row for a global index (-1 if none).
-  //   C[0]: [W0][N1][N2]   C[1]: [N0][W1][N2]   C[2]: [N0][N1][W2],  Wd = S_d * 2t
-  const int* kf[3];
-  const int* kl[3];
-  float2* C[3];
-  int Wd[3];
 };
 
 // Device-side solver state (one per plan). Every iteration kernel leaves at once
@@ -68,7 +60,8 @@ enum MidMode { MID_PROP = 0, MID_LSYM = 1, MID_FWD = 2, MID_INV = 3 };
 enum ShellMode { SHELL_UPDATE_ITER = 1, SHELL_UPDATE_PRECOND = 2, SHELL_ADD_E = 3, SHELL_SET_E = 4 };
 
 struct PassArgs {
-  float2* K;            // FFT buffer
+  float2* K;            // FFT buffer (on entry of the first pass: E x on the boundary layers)
+  float2* E;            // e = x - w on the boundary layers (written by the last pass)
   const float2* X;      // field input
   float2* Xout;         // updated field or operator output
   const float2* B;      // medium factor 1 - c(k^2 - k0^2)
@@ -88,9 +81,12 @@ struct PassArgs {
   int subs[kMaxSplit];
 };
 
-// Edge corrections E_d F of one axis into the slab C[d] (Sec. 3.1 steps 1-2, 4-5).
+// Edge corrections E_d F of one axis, written (or, where an earlier axis has
+// already written that voxel, added) into the full-size buffer C at the
+// boundary-layer voxels (Sec. 3.1 steps 1-2, 4-5). Axes run in order 0, 1, 2.
 struct CorrArgs {
   const float2* F;      // field the corrections are taken of
+  float2* C;            // correction buffer (only boundary-layer voxels are written)
   const float2* cW;     // c * W, t x t, row-major
   AxisTables tb;
   GridDesc g;
@@ -98,9 +94,10 @@ struct CorrArgs {
   int axis;
 };
 
-// Voxels of the boundary layers: sum of the slabs, then the mode's update.
+// Voxels of the boundary layers: E = C[v], then the mode's update.
 struct ShellArgs {
   const float2* E;      // e = x - w on the layers (UPDATE modes)
+  const float2* C;      // corrections (E e or E x) on the layers
   float2* X;            // field (updated in UPDATE_ITER)
   float2* out;          // operator output
   const float2* B;

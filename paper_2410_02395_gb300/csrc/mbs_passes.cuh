@@ -18,7 +18,6 @@
 #pragma once
 #include "mbs_fft.cuh"
 #include "mbs_internal.h"
-#include "mbs_slab.cuh"
 
 namespace mbs {
 
@@ -48,10 +47,14 @@ __device__ __forceinline__ float2 (*tile_of(float2* dyn))[kPad] {
 // ---------------------------------------------------------------------------
 struct RowInfo {
   long long base;  // global index of element 0 of the segment
-  long long i0, i1;
   int flags;       // bit0 valid, bit1 row inside an axis-0/1 boundary layer, bit2 row inside the source box
-  RowSlab rs;
 };
+
+// Element e of an axis-2 segment of length N lies in a boundary layer of that axis.
+template <int N>
+__device__ __forceinline__ bool in_layer2(const PassArgs& a, int e) {
+  return a.g.ax[2].a > 0 && (e < a.g.t || e >= N - a.g.t);
+}
 
 __device__ __forceinline__ void setup_rows(RowInfo* ri, const PassArgs& a, int off2) {
   const int tid = threadIdx.x;
@@ -61,16 +64,12 @@ __device__ __forceinline__ void setup_rows(RowInfo* ri, const PassArgs& a, int o
     RowInfo r;
     r.flags = 0;
     r.base = 0;
-    r.i0 = r.i1 = 0;
-    r.rs = RowSlab{-1, -1, -1, -1};
     if (rho < rows) {
-      r.i0 = rho / a.g.N1;
-      r.i1 = rho - r.i0 * a.g.N1;
+      const long long i0 = rho / a.g.N1, i1 = rho - i0 * a.g.N1;
       r.base = rho * a.g.N2 + off2;
       r.flags = 1;
-      if (a.tb.shell[0][r.i0] | a.tb.shell[1][r.i1]) r.flags |= 2;
-      if (a.S && r.i0 >= a.sbox[0] && r.i0 < a.sbox[1] && r.i1 >= a.sbox[2] && r.i1 < a.sbox[3]) r.flags |= 4;
-      r.rs = row_slab(a.tb, r.i0, r.i1);
+      if (a.tb.shell[0][i0] | a.tb.shell[1][i1]) r.flags |= 2;
+      if (a.S && i0 >= a.sbox[0] && i0 < a.sbox[1] && i1 >= a.sbox[2] && i1 < a.sbox[3]) r.flags |= 4;
     }
     ri[tid] = r;
   }
@@ -98,19 +97,23 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_rows_first(const __grid_c
   const bool iter = a.mode == FIRST_ITER;
   const float2* __restrict__ X = a.X;
   const float2* __restrict__ B = a.B;
+  float2* K = a.K;
   for (int k0 = 0; k0 < PERT; k0 += CH) {
-    float2 xv[CH], bv[CH];
+    float2 xv[CH], bv[CH], cv[CH];
 #pragma unroll
     for (int c = 0; c < CH; c++) {
       const int idx = tid + (k0 + c) * NT;
-      xv[c] = make_float2(0.f, 0.f);
-      bv[c] = make_float2(0.f, 0.f);
+      xv[c] = bv[c] = cv[c] = make_float2(0.f, 0.f);
       if (idx < 32 * N) {
         const int r = idx / N, e = idx - r * N;
-        if (ri[r].flags & 1) {
+        const int f = ri[r].flags;
+        if (f & 1) {
           const long long gi = ri[r].base + e;
           xv[c] = __ldg(X + gi);
-          if (iter) bv[c] = __ldg(B + gi);
+          if (iter) {
+            bv[c] = __ldg(B + gi);
+            if ((f & 2) || in_layer2<N>(a, e)) cv[c] = K[gi];  // E x on the boundary layers
+          }
         }
       }
     }
@@ -122,10 +125,8 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_rows_first(const __grid_c
         const int f = ri[r].flags;
         float2 u = xv[c];
         if (iter && (f & 1)) {
-          u = cmul(bv[c], xv[c]);
+          u = csub(cmul(bv[c], xv[c]), cv[c]);
           const long long i2 = off2 + e;
-          if ((f & 2) || a.tb.shell[2][i2])
-            u = csub(u, slab_sum(a.tb, a.g, ri[r].rs, ri[r].i0, ri[r].i1, ri[r].i0 * a.g.N1 + ri[r].i1, i2));
           if ((f & 4) && i2 >= a.sbox[4] && i2 < a.sbox[5]) u = cadd(u, cmul(a.mc, a.S[ri[r].base + e]));
         }
         sm[e][r] = u;
@@ -139,7 +140,6 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_rows_first(const __grid_c
     fft_run<N, W, false, false, 0, 1, true, true>(warp, lane, sm, a.tw, sld, sst);
   }
   __syncthreads();
-  float2* K = a.K;
   for (int k0 = 0; k0 < PERT; k0++) {
     const int idx = tid + k0 * NT;
     if (idx < 32 * N) {
@@ -235,8 +235,8 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_rows_last(const __grid_co
         a.Xout[gi] = cadd(w, cmul(make_float2(1.f - bv[c].x, -bv[c].y), xv[c]));
       } else {
         const float2 ee = csub(xv[c], w);
-        if ((f & 2) || a.tb.shell[2][off2 + e]) {
-          K[gi] = ee;  // finished by the layer update once all of e is known
+        if ((f & 2) || in_layer2<N>(a, e)) {
+          a.E[gi] = ee;  // finished by the layer update once all of e is known
         } else {
           const float2 rr = cmul(bv[c], ee);
           acc += (double)rr.x * rr.x + (double)rr.y * rr.y;
