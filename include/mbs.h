@@ -73,7 +73,7 @@ typedef enum mbs_operator {
 
 /* Limits of this build. */
 #define MBS_MAX_SPLIT 16 /* subdomains per axis */
-#define MBS_MAX_T 32     /* truncation width */
+#define MBS_MAX_T 32     /* truncation width; compiled values t = 1..16, 20, 24, 32 */
 #define MBS_MAX_EDGE 512 /* longest subdomain edge; edges must factor into 2, 3, 5, 7 */
 
 /* Option flags. */

@@ -249,6 +249,7 @@ mbs_status validate_and_fill(mbs_plan* p, const int64_t shape[3], double h, doub
   p->t = (o && o->truncation > 0) ? o->truncation : 8;
   if (o && o->truncation < 0) return fail(MBS_EINVAL, "truncation must be >= 0");
   if (p->t > kMaxT) return fail(MBS_EINVAL, "truncation exceeds MBS_MAX_T");
+  if (!corr_t_supported(p->t)) return fail(MBS_EUNSUPPORTED, "truncation t must be 1..16, 20, 24 or 32");
   p->alpha = (o && o->alpha > 0.0) ? o->alpha : 0.75;
   p->kappa = (o && o->absorb_kappa >= 0.0) ? o->absorb_kappa : 0.5;
   p->periodic = o ? o->periodic_mask : 0u;

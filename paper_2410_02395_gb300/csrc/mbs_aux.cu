@@ -23,15 +23,27 @@ __device__ __forceinline__ void put(float2* C, long long v, float2 val, bool add
   C[v] = add ? cadd(C[v], val) : val;
 }
 
+// W is Toeplitz, W[a][b] = D(t + b - a): its 2t - 1 distinct entries c*D(1..2t-1)
+// are cw[m] = cW[0][m - t + 1]... indexed here by b - a + t - 1.
+template <int T>
+__device__ __forceinline__ void load_toeplitz(const float2* __restrict__ cW, float2 (&w)[2 * T - 1]) {
+#pragma unroll
+  for (int m = 0; m < 2 * T - 1; m++) {
+    // b - a = m - (T - 1): take row a = max(0, T-1-m), column b = a + m - (T - 1)
+    const int aa = m < T - 1 ? T - 1 - m : 0;
+    const int bb = aa + m - (T - 1);
+    w[m] = __ldg(cW + aa * T + bb);
+  }
+}
+
 // Axes 0 and 1: one thread per (pencil, subdomain); consecutive threads take
 // consecutive axis-2 positions, so every load and store is coalesced.
-template <int TM>
+template <int T>
 __global__ void __launch_bounds__(128) k_corr_strided(const __grid_constant__ CorrArgs a) {
   if (a.state && a.state->done) return;
   const int d = a.axis;
   const AxisDesc& ax = a.g.ax[d];
   const long long N0 = a.g.N0, N1 = a.g.N1, N2 = a.g.N2;
-  const int t = a.g.t;
   const long long npen = d == 0 ? N1 * N2 : N0 * N2;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= npen * ax.S) return;
@@ -51,93 +63,102 @@ __global__ void __launch_bounds__(128) k_corr_strided(const __grid_constant__ Co
   const int off = ax.off[s], n = ax.n[s];
   const int L = ax.left[s], R = ax.right[s];
   const float2* __restrict__ F = a.F;
-  float2 D[TM], E[TM];
+  float2 D[T], E[T];
 #pragma unroll
-  for (int b = 0; b < TM; b++) {
-    if (b < t) {
-      const float2 A = F[base + (long long)(off + b) * stride];
-      const float2 Z = F[base + (long long)(off + n - t + b) * stride];
-      const float2 Rv = R >= 0 ? F[base + (long long)(ax.off[R] + b) * stride] : make_float2(0.f, 0.f);
-      const float2 Lv = L >= 0 ? F[base + (long long)(ax.off[L] + ax.n[L] - t + b) * stride] : make_float2(0.f, 0.f);
-      D[b] = csub(Rv, A);
-      E[b] = csub(Lv, Z);
-    } else {
-      D[b] = E[b] = make_float2(0.f, 0.f);
-    }
+  for (int b = 0; b < T; b++) {
+    const float2 A = F[base + (long long)(off + b) * stride];
+    const float2 Z = F[base + (long long)(off + n - T + b) * stride];
+    const float2 Rv = R >= 0 ? F[base + (long long)(ax.off[R] + b) * stride] : make_float2(0.f, 0.f);
+    const float2 Lv = L >= 0 ? F[base + (long long)(ax.off[L] + ax.n[L] - T + b) * stride] : make_float2(0.f, 0.f);
+    D[b] = csub(Rv, A);
+    E[b] = csub(Lv, Z);
   }
-  const float2* __restrict__ cW = a.cW;
-  auto last_val = [&](int aa) {
+  float2 w[2 * T - 1];
+  load_toeplitz<T>(a.cW, w);
+  float2* C = a.C;
+  // first t layers: (W^T E)[q] = sum_b W[b][q] E[b] = sum_b w[q - b + T - 1] E[b]
+  float2 outf[T];
+#pragma unroll
+  for (int q = 0; q < T; q++) {
     float2 v = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int b = 0; b < TM; b++)
-      if (b < t) v = cadd(v, cmul(__ldg(cW + aa * t + b), D[b]));
-    return v;
-  };
-  float2* C = a.C;
+    for (int b = 0; b < T; b++) v = cadd(v, cmul(w[q - b + T - 1], E[b]));
+    outf[q] = v;
+  }
+  // last t layers: (W D)[aa] = sum_b W[aa][b] D[b] = sum_b w[b - aa + T - 1] D[b]
 #pragma unroll
-  for (int q = 0; q < TM; q++) {  // first t layers (q < t), plus the last-range term if they overlap
-    if (q < t) {
-      float2 v = make_float2(0.f, 0.f);
+  for (int aa = 0; aa < T; aa++) {
+    float2 v = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int b = 0; b < TM; b++)
-        if (b < t) v = cadd(v, cmul(__ldg(cW + b * t + q), E[b]));
-      if (q >= n - t) v = cadd(v, last_val(q - (n - t)));
+    for (int b = 0; b < T; b++) v = cadd(v, cmul(w[b - aa + T - 1], D[b]));
+    const int q = n - T + aa;
+    if (q < T) {
+      outf[q] = cadd(outf[q], v);  // n < 2t: the voxel is in both ranges (q == n - T + aa)
+    } else {
       put(C, base + (long long)(off + q) * stride, v, add);
     }
   }
 #pragma unroll
-  for (int aa = 0; aa < TM; aa++) {  // last t layers not already written above
-    const int q = n - t + aa;
-    if (aa < t && q >= t) put(C, base + (long long)(off + q) * stride, last_val(aa), add);
-  }
+  for (int q = 0; q < T; q++) put(C, base + (long long)(off + q) * stride, outf[q], add);
 }
 
 // Axis 2: one warp per grid row; the row's 2t layer values of every subdomain
 // are staged in shared memory with coalesced loads, then each lane produces
 // outputs from shared memory.
+template <int T>
 __global__ void __launch_bounds__(256) k_corr_rows(const __grid_constant__ CorrArgs a) {
   extern __shared__ float2 cs[];
   if (a.state && a.state->done) return;
   const AxisDesc& ax = a.g.ax[2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int t = a.g.t, S = ax.S, M = S * 2 * t;
+  const int S = ax.S, M = S * 2 * T;
   float2* sm = cs + warp * M;
   const long long N1 = a.g.N1, N2 = a.g.N2, rows = a.g.N0 * N1;
   const float2* __restrict__ F = a.F;
-  const float2* __restrict__ cW = a.cW;
+  __shared__ float2 w[2 * T - 1];  // lanes index it with their own (runtime) output position
+  if (threadIdx.x == 0) {
+    float2 wr[2 * T - 1];
+    load_toeplitz<T>(a.cW, wr);
+#pragma unroll
+    for (int m = 0; m < 2 * T - 1; m++) w[m] = wr[m];
+  }
+  __syncthreads();
   float2* C = a.C;
   for (long long rho = (long long)blockIdx.x * 8 + warp; rho < rows; rho += (long long)gridDim.x * 8) {
     const long long i0 = rho / N1, i1 = rho - i0 * N1;
     const bool add = a.tb.shell[0][i0] || a.tb.shell[1][i1];
     const long long rb = rho * N2;
     for (int idx = lane; idx < M; idx += 32) {
-      const int s = idx / (2 * t), k = idx - s * 2 * t;
-      const int q = k < t ? k : ax.n[s] - t + (k - t);
+      const int s = idx / (2 * T), k = idx - s * 2 * T;
+      const int q = k < T ? k : ax.n[s] - T + (k - T);
       sm[idx] = F[rb + ax.off[s] + q];
     }
     __syncwarp();
     for (int idx = lane; idx < M; idx += 32) {
-      const int s = idx / (2 * t), k = idx - s * 2 * t;
+      const int s = idx / (2 * T), k = idx - s * 2 * T;
       const int n = ax.n[s];
-      const float2* own = sm + s * 2 * t;  // own[0..t): first t layers, own[t..2t): last t layers
-      const float2* lf = ax.left[s] >= 0 ? sm + ax.left[s] * 2 * t + t : nullptr;
-      const float2* rf = ax.right[s] >= 0 ? sm + ax.right[s] * 2 * t : nullptr;
+      const float2* own = sm + s * 2 * T;  // own[0..t): first t layers, own[t..2t): last t layers
+      const int lft = ax.left[s], rgt = ax.right[s];
       // local position q of this output; in the last range, voxels that are also
       // in the first range (n < 2t) are produced by the first-range lane
-      const int q = k < t ? k : n - t + (k - t);
-      if (k >= t && q < t) continue;
+      const int q = k < T ? k : n - T + (k - T);
+      if (k >= T && q < T) continue;
       float2 v = make_float2(0.f, 0.f);
-      if (q < t) {  // first t layers: row q of W^T on (left's last t - own last t)
-        for (int b = 0; b < t; b++) {
-          const float2 f = lf ? csub(lf[b], own[t + b]) : make_float2(-own[t + b].x, -own[t + b].y);
-          v = cadd(v, cmul(__ldg(cW + b * t + q), f));
+      if (q < T) {  // first t layers: row q of W^T on (left's last t - own last t)
+#pragma unroll
+        for (int b = 0; b < T; b++) {
+          float2 f = make_float2(-own[T + b].x, -own[T + b].y);
+          if (lft >= 0) f = cadd(f, sm[lft * 2 * T + T + b]);
+          v = cadd(v, cmul(w[q - b + T - 1], f));
         }
       }
-      if (q >= n - t) {  // last t layers: row q-(n-t) of W on (right's first t - own first t)
-        const int aa = q - (n - t);
-        for (int b = 0; b < t; b++) {
-          const float2 f = rf ? csub(rf[b], own[b]) : make_float2(-own[b].x, -own[b].y);
-          v = cadd(v, cmul(__ldg(cW + aa * t + b), f));
+      if (q >= n - T) {  // last t layers: row q-(n-t) of W on (right's first t - own first t)
+        const int aa = q - (n - T);
+#pragma unroll
+        for (int b = 0; b < T; b++) {
+          float2 f = make_float2(-own[b].x, -own[b].y);
+          if (rgt >= 0) f = cadd(f, sm[rgt * 2 * T + b]);
+          v = cadd(v, cmul(w[b - aa + T - 1], f));
         }
       }
       put(C, rb + ax.off[s] + q, v, add);
@@ -146,31 +167,40 @@ __global__ void __launch_bounds__(256) k_corr_rows(const __grid_constant__ CorrA
   }
 }
 
-cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st) {
+template <int T>
+cudaError_t launch_corr_t(const CorrArgs& a, cudaStream_t st) {
   const AxisDesc& ax = a.g.ax[a.axis];
-  const int t = a.g.t;
   if (a.axis == 2) {
-    const size_t smem = (size_t)8 * ax.S * 2 * t * sizeof(float2);
+    const size_t smem = (size_t)8 * ax.S * 2 * T * sizeof(float2);
     if (smem > 48 * 1024) {
-      const cudaError_t e = cudaFuncSetAttribute(k_corr_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      const cudaError_t e = cudaFuncSetAttribute(k_corr_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e) return e;
     }
     const long long rows = a.g.N0 * a.g.N1;
     const long long blocks = (rows + 7) / 8 < 152 * 16 ? (rows + 7) / 8 : 152 * 16;
-    k_corr_rows<<<(unsigned)blocks, 256, smem, st>>>(a);
+    k_corr_rows<T><<<(unsigned)blocks, 256, smem, st>>>(a);
     return cudaGetLastError();
   }
   const long long npen = a.axis == 0 ? a.g.N1 * a.g.N2 : a.g.N0 * a.g.N2;
   const unsigned blocks = (unsigned)((npen * ax.S + 127) / 128);
-  if (t <= 4)
-    k_corr_strided<4><<<blocks, 128, 0, st>>>(a);
-  else if (t <= 8)
-    k_corr_strided<8><<<blocks, 128, 0, st>>>(a);
-  else if (t <= 16)
-    k_corr_strided<16><<<blocks, 128, 0, st>>>(a);
-  else
-    k_corr_strided<32><<<blocks, 128, 0, st>>>(a);
+  k_corr_strided<T><<<blocks, 128, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+bool corr_t_supported(int t) { return (t >= 1 && t <= 16) || t == 20 || t == 24 || t == 32; }
+
+cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st) {
+  switch (a.g.t) {
+#define MBS_T(T) \
+  case T:        \
+    return launch_corr_t<T>(a, st);
+    MBS_T(1) MBS_T(2) MBS_T(3) MBS_T(4) MBS_T(5) MBS_T(6) MBS_T(7) MBS_T(8)
+    MBS_T(9) MBS_T(10) MBS_T(11) MBS_T(12) MBS_T(13) MBS_T(14) MBS_T(15) MBS_T(16)
+    MBS_T(20) MBS_T(24) MBS_T(32)
+#undef MBS_T
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 __device__ __forceinline__ double block_sum_all(double v, double* red) {
@@ -191,7 +221,7 @@ __device__ __forceinline__ double block_sum_all(double v, double* red) {
 //   UPDATE_ITER:    r = B e - E, x <- x - alpha r, FP64 |r|^2   (e from the last pass)
 //   UPDATE_PRECOND: out = -(B e - E)
 //   ADD_E:          out += E          SET_E: out = E
-// Each lane handles up to 8 voxels of a row per round with all loads issued first.
+// Each lane handles up to 4 voxels of a row per round with all loads issued first.
 __global__ void __launch_bounds__(256) k_shell(const __grid_constant__ ShellArgs a) {
   __shared__ double red[8];
   if (a.state && a.state->done) return;
@@ -200,8 +230,8 @@ __global__ void __launch_bounds__(256) k_shell(const __grid_constant__ ShellArgs
   const long long rows = a.g.N0 * N1;
   const int mode = a.mode;
   const bool upd = mode == SHELL_UPDATE_ITER || mode == SHELL_UPDATE_PRECOND;
-  constexpr int U = 8;
-  double acc = 0.0;
+  constexpr int U = 4;
+  double acc = 0.0;  // FP64 across rounds; each round's (<= U voxels) partial is FP32
   for (long long rho = (long long)blockIdx.x * 8 + warp; rho < rows; rho += (long long)gridDim.x * 8) {
     const long long i0 = rho / N1, i1 = rho - i0 * N1;
     const bool full = a.tb.shell[0][i0] || a.tb.shell[1][i1];
@@ -226,12 +256,13 @@ __global__ void __launch_bounds__(256) k_shell(const __grid_constant__ ShellArgs
           }
         }
       }
+      float racc = 0.f;
 #pragma unroll
       for (int u = 0; u < U; u++) {
         if (v[u] < 0) continue;
         if (upd) {
           const float2 r = csub(cmul(bv[u], ev[u]), cv[u]);
-          acc += (double)r.x * r.x + (double)r.y * r.y;
+          racc = fmaf(r.x, r.x, fmaf(r.y, r.y, racc));
           if (mode == SHELL_UPDATE_ITER)
             a.X[v[u]] = make_float2(fmaf(-a.alpha, r.x, xv[u].x), fmaf(-a.alpha, r.y, xv[u].y));
           else
@@ -242,6 +273,7 @@ __global__ void __launch_bounds__(256) k_shell(const __grid_constant__ ShellArgs
           a.out[v[u]] = cv[u];
         }
       }
+      acc += (double)racc;
     }
   }
   if (a.partials) {

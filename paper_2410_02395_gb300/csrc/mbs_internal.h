@@ -117,6 +117,7 @@ cudaError_t launch_mid(int n, const PassArgs& a, cudaStream_t st);
 bool fft_size_compiled(int n);
 
 cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st);
+bool corr_t_supported(int t);
 cudaError_t launch_shell(const ShellArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_finalize(DevState* state, const double* p1, int n1, const double* p2, int n2, double* history,
                             cudaStream_t st);

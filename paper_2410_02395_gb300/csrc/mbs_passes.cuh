@@ -34,6 +34,12 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// Resident CTAs per SM asked of the register allocator: 32 warps per SM, i.e.
+// at most 64 registers per thread (the tiles of that many CTAs fit in 228 KB).
+__host__ __device__ constexpr int fft_min_blocks(int n) {
+  return 32 / warps_for(n) > 1 ? 32 / warps_for(n) : 1;
+}
+
 template <int N>
 __device__ __forceinline__ float2 (*tile_of(float2* dyn))[kPad] {
   return reinterpret_cast<float2 (*)[kPad]>(dyn);
@@ -80,7 +86,7 @@ __device__ __forceinline__ void setup_rows(RowInfo* ri, const PassArgs& a, int o
 // u = B x + y - E x (FIRST_ITER) or u = x (FIRST_PLAIN), then the transform.
 // ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(32 * warps_for(N)) k_rows_first(const __grid_constant__ PassArgs a) {
+__global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_first(const __grid_constant__ PassArgs a) {
   constexpr int W = warps_for(N);
   constexpr int NT = 32 * W;
   constexpr int PERT = (32 * N + NT - 1) / NT;
@@ -155,7 +161,7 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_rows_first(const __grid_c
 // FP64 |r|^2; on the layers e is stored for the correction step.
 // ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(32 * warps_for(N)) k_rows_last(const __grid_constant__ PassArgs a) {
+__global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_last(const __grid_constant__ PassArgs a) {
   constexpr int W = warps_for(N);
   constexpr int NT = 32 * W;
   constexpr int PERT = (32 * N + NT - 1) / NT;
@@ -198,7 +204,9 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_rows_last(const __grid_co
     fft_run<N, W, true, false, 0, 1, true, true>(warp, lane, sm, a.tw, sld, sst);
   }
   __syncthreads();
-  double acc = 0.0;
+  // |r|^2 of this thread's (at most N/W) voxels in FP32, then FP64 across threads
+  // and blocks: GB300's FP64 rate is too low for a per-voxel FP64 accumulation.
+  float acc = 0.f;
   const int mode = a.mode;
   const float2* X = a.X;
   const float2* __restrict__ B = a.B;
@@ -239,7 +247,7 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_rows_last(const __grid_co
           a.E[gi] = ee;  // finished by the layer update once all of e is known
         } else {
           const float2 rr = cmul(bv[c], ee);
-          acc += (double)rr.x * rr.x + (double)rr.y * rr.y;
+          acc = fmaf(rr.x, rr.x, fmaf(rr.y, rr.y, acc));
           a.Xout[gi] = (mode == LAST_ITER) ? make_float2(fmaf(-a.alpha, rr.x, xv[c].x), fmaf(-a.alpha, rr.y, xv[c].y))
                                            : make_float2(-rr.x, -rr.y);
         }
@@ -247,7 +255,7 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_rows_last(const __grid_co
     }
   }
   if (a.partials) {
-    const double s = block_sum(acc, red);
+    const double s = block_sum((double)acc, red);
     if (tid == 0) a.partials[blockIdx.x + (long long)gridDim.x * blockIdx.y] = s;
   }
 }
@@ -256,7 +264,7 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_rows_last(const __grid_co
 // Axis-1 / axis-0 transform of a tile of 32 consecutive axis-2 positions.
 // ---------------------------------------------------------------------------
 template <int N, int AXIS, bool INV>
-__global__ void __launch_bounds__(32 * warps_for(N)) k_strided(const __grid_constant__ PassArgs a) {
+__global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_strided(const __grid_constant__ PassArgs a) {
   constexpr int W = warps_for(N);
   extern __shared__ float2 dyn[];
   float2 (*sm)[kPad] = tile_of<N>(dyn);
@@ -345,7 +353,7 @@ __global__ void __launch_bounds__(32 * warps_for(N), MIN_BLOCKS) k_mid_turn(cons
 
 // Forward-only (MID_FWD) or scaled inverse-only (MID_INV) axis-0 transform.
 template <int N>
-__global__ void __launch_bounds__(32 * warps_for(N)) k_mid_plain(const __grid_constant__ PassArgs a) {
+__global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_mid_plain(const __grid_constant__ PassArgs a) {
   constexpr int W = warps_for(N);
   extern __shared__ float2 dyn[];
   float2 (*sm)[kPad] = tile_of<N>(dyn);
@@ -374,15 +382,20 @@ __global__ void __launch_bounds__(32 * warps_for(N)) k_mid_plain(const __grid_co
 // ---------------------------------------------------------------------------
 inline size_t tile_bytes(int n) { return (size_t)n * kPad * sizeof(float2); }
 
-// Resident CTAs per SM asked of the register allocator for the axis-0 pass.
-constexpr int mid_min_blocks(int n) { return n >= 64 && n <= 256 ? 3 : 1; }
+// Resident CTAs per SM asked of the register allocator for the axis-0 pass
+// (forward + multiplier + inverse keeps more values live than a single pass).
+constexpr int mid_min_blocks(int n) { return 24 / warps_for(n) > 1 ? 24 / warps_for(n) : 1; }
 
-// Opt in to more than 48 KB of dynamic shared memory once per kernel.
+// Once per kernel: the largest shared-memory carveout (several tiles per SM)
+// and, above 48 KB, the dynamic shared-memory opt-in.
 template <class K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
   static bool done = false;
-  if (bytes <= 48 * 1024 || done) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess && bytes > 48 * 1024)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) done = true;
   return e;
 }
