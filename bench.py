@@ -40,21 +40,29 @@ METRIC = "voxel-iterations/s on 1 GB300 (mixed vs plain FP32, ≤1e-4 vs FP64); 
 UNIT = "voxel-iterations/s"
 
 # Algorithmic bytes per voxel and iteration of each kernel kind (summed over its
-# launches in one iteration; complex64 = 8 B). L = sum over corrected axes of the
-# layer fraction 2t*S_d/N_d, sh = fraction of voxels in any boundary layer.
-def kernel_bytes_per_voxel(kind, L, sh):
+# launches in one iteration; complex64 = 8 B). fr holds layer fractions:
+#   L   = sum over corrected axes of 2t*S_d/N_d,  L01 the same over axes 0 and 1,
+#   sh  = fraction of voxels in any boundary layer, g01 = in an axis-0/1 layer.
+def kernel_bytes_per_voxel(kind, fr):
     f = 8.0
     return {
-        "corr_x": 2 * L * f,                   # each axis's layers in, its correction slab out
-        "rows_first": 3 * f + L * f,           # x, B in, FFT buffer out, slabs in
+        "corr_x": 2 * fr["L01"] * f,           # axis-0/1 layers of x in, E x out on them
+        "rows_first": 3 * f + fr["g01"] * f,   # x, B in, FFT buffer out, E_0 x + E_1 x in on those rows
         "strided_fwd": 2 * f,
         "mid_axis0": 2 * f,
         "strided_inv": 2 * f,
         "rows_last": 4 * f,                    # FFT buffer, x, B in; x (or e on the layers) out
-        "corr_e": 2 * L * f,
-        "shell_update": 4 * sh * f + L * f,    # e, x, B in and x out on the layers; slabs in
-        "finalize": 0.0,
+        "corr_e": 2 * fr["L"] * f,             # layers of e in, E e out on them
+        "shell_update": 5 * fr["sh"] * f,      # e, E e, x, B in and x out on the layer voxels
     }[kind]
+
+
+def layer_fractions(info):
+    t = info["t"]
+    fd = [min(1.0, 2.0 * t * len(s) / sum(s)) if info["a"][d] > 0 else 0.0 for d, s in enumerate(info["sizes"])]
+    sh = 1.0 - (1.0 - fd[0]) * (1.0 - fd[1]) * (1.0 - fd[2])
+    g01 = 1.0 - (1.0 - fd[0]) * (1.0 - fd[1])
+    return {"L": sum(fd), "L01": fd[0] + fd[1], "sh": sh, "g01": g01}
 
 
 def read_peaks():
@@ -263,23 +271,17 @@ def main():
         launches_per_iter = sum(v[0] for v in prof.values()) / K
         tot = sum(v[1] for v in prof.values())
         dom = max(prof, key=lambda k: prof[k][1])
-        t = info["t"]
-        layer = sum(min(1.0, 2.0 * t * len(s) / sum(s)) for d, s in enumerate(info["sizes"]) if info["a"][d] > 0)
-        inner = 1.0
-        for d, s in enumerate(info["sizes"]):
-            if info["a"][d] > 0:
-                inner *= max(0.0, 1.0 - 2.0 * t * len(s) / sum(s))
-        shell = 1.0 - inner
+        fr = layer_fractions(info)
         peak, peak_src = read_peaks()
         dom_launches, dom_ms = prof[dom]
-        bytes_per_launch = kernel_bytes_per_voxel(dom, layer, shell) * vox / max(1.0, dom_launches / K)
+        bytes_per_launch = kernel_bytes_per_voxel(dom, fr) * vox / max(1.0, dom_launches / K)
         achieved = bytes_per_launch / (dom_ms / dom_launches / 1e3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": None, "kernel": dom, "peak_source": peak_src,
                     "share": prof[dom][1] / tot if tot else None,
                     "bytes_per_launch": bytes_per_launch,
                     "kernels": {k: {"launches": v[0], "ms_per_iter": v[1] / K,
-                                    "GBps": (kernel_bytes_per_voxel(k, layer, shell) * vox * K / (v[1] / 1e3) / 1e9)
+                                    "GBps": (kernel_bytes_per_voxel(k, fr) * vox * K / (v[1] / 1e3) / 1e9)
                                     if v[1] > 0 else None} for k, v in prof.items()}}
 
         # ---- end to end through the C ABI with pinned host buffers ------------

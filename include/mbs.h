@@ -193,7 +193,7 @@ MBS_API mbs_status mbs_solve(mbs_plan *plan, const void *source, void *out, doub
  * kernel kind the number of launches and the summed device milliseconds.
  * kind names: mbs_kernel_kind_name(i) for i < MBS_KERNEL_KINDS.
  */
-#define MBS_KERNEL_KINDS 9
+#define MBS_KERNEL_KINDS 8
 MBS_API mbs_status mbs_profile_iterations(mbs_plan *plan, int32_t n_iter, int32_t launches[MBS_KERNEL_KINDS],
                                   double ms[MBS_KERNEL_KINDS]);
 MBS_API const char *mbs_kernel_kind_name(int32_t kind);

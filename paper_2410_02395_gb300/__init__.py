@@ -24,7 +24,7 @@ STATUS = {0: "MBS_OK", 1: "MBS_EINVAL", 2: "MBS_ENOMEM", 3: "MBS_ECUDA", 4: "MBS
           6: "MBS_EDIVERGE", 7: "MBS_ETIMEOUT", 8: "MBS_EUNSUPPORTED"}
 OP = {"A": 0, "PRECOND": 1, "V": 2, "L": 3, "PROPAGATE": 4, "E": 5, "FFT": 6, "IFFT": 7}
 MAX_SPLIT = 16
-KERNEL_KINDS = 9
+KERNEL_KINDS = 8
 
 
 class MBSError(RuntimeError):

@@ -443,6 +443,7 @@ PassArgs base_args(mbs_plan* p) {
   a.ck0 = make_float2((float)ck0r, (float)ck0i);
   a.mc = make_float2((float)-p->c_re, (float)-p->c_im);
   a.alpha = (float)p->alpha;
+  a.cW = p->cW;
   a.tb = p->tb;
   a.g = p->g;
   return a;
@@ -462,13 +463,12 @@ ShellArgs shell_args(mbs_plan* p) {
 }
 
 // Edge corrections E F into the buffer C at the boundary-layer voxels.
-cudaError_t run_corr(mbs_plan* p, const float2* F, float2* C, const DevState* state);
+cudaError_t run_corr(mbs_plan* p, const float2* F, float2* C, const DevState* state, bool axis2 = true);
 
 int nrow_blocks(const mbs_plan* p) { return (int)((p->N[0] * p->N[1] + 31) / 32); }
 
 // Kernel kinds for profiling.
-enum { KK_CORR_X = 0, KK_ROWS_FIRST, KK_STRIDED_FWD, KK_MID, KK_STRIDED_INV, KK_ROWS_LAST, KK_CORR_E, KK_SHELL_UPDATE,
-       KK_FINALIZE };
+enum { KK_CORR_X = 0, KK_ROWS_FIRST, KK_STRIDED_FWD, KK_MID, KK_STRIDED_INV, KK_ROWS_LAST, KK_CORR_E, KK_SHELL_UPDATE };
 
 struct Recorder {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>* ev = nullptr;
@@ -489,7 +489,8 @@ struct Recorder {
   }
 };
 
-cudaError_t run_corr_rec(mbs_plan* p, const float2* F, float2* C, const DevState* state, Recorder* rec, int kind) {
+cudaError_t run_corr_rec(mbs_plan* p, const float2* F, float2* C, const DevState* state, Recorder* rec, int kind,
+                         bool axis2) {
   CorrArgs c;
   memset(&c, 0, sizeof(c));
   c.F = F;
@@ -498,7 +499,7 @@ cudaError_t run_corr_rec(mbs_plan* p, const float2* F, float2* C, const DevState
   c.tb = p->tb;
   c.g = p->g;
   c.state = state;
-  for (int d = 0; d < 3; d++) {
+  for (int d = 0; d < (axis2 ? 3 : 2); d++) {
     if (!(p->t > 0 && p->a[d] > 0)) continue;
     c.axis = d;
     if (rec) rec->begin(kind);
@@ -509,8 +510,8 @@ cudaError_t run_corr_rec(mbs_plan* p, const float2* F, float2* C, const DevState
   return cudaSuccess;
 }
 
-cudaError_t run_corr(mbs_plan* p, const float2* F, float2* C, const DevState* state) {
-  return run_corr_rec(p, F, C, state, nullptr, 0);
+cudaError_t run_corr(mbs_plan* p, const float2* F, float2* C, const DevState* state, bool axis2) {
+  return run_corr_rec(p, F, C, state, nullptr, 0, axis2);
 }
 
 // The forward half shared by the iteration and several operators:
@@ -562,15 +563,21 @@ cudaError_t run_transform_chain(mbs_plan* p, PassArgs a, int first_mode, int mid
   return cudaSuccess;
 }
 
-cudaError_t run_rows_last(mbs_plan* p, PassArgs a, int mode, bool partials, Recorder* rec) {
+// fin: the last launch ends the iteration (no boundary-layer kernel follows).
+cudaError_t run_rows_last(mbs_plan* p, PassArgs a, int mode, bool partials, Recorder* rec, bool fin = false) {
   const int nrb = nrow_blocks(p);
   a.mode = mode;
   int poff = 0;
-  for (auto& gz : p->groups[2]) {
+  for (size_t gi = 0; gi < p->groups[2].size(); gi++) {
+    auto& gz = p->groups[2][gi];
     a.nsub = gz.nsub;
     memcpy(a.subs, gz.subs, sizeof(a.subs));
     a.tw = p->tw[gz.n];
-    a.partials = partials ? p->partials + poff : nullptr;
+    a.partials = partials ? p->partials : nullptr;
+    a.slot0 = poff;
+    a.n_total = p->n_rows_partials + (p->has_shell ? kShellBlocks : 0);
+    a.fin = (fin && gi + 1 == p->groups[2].size()) ? p->state : nullptr;
+    a.hist = p->history;
     poff += nrb * gz.nsub;
     if (rec) rec->begin(KK_ROWS_LAST);
     cudaError_t e = launch_rows_last(gz.n, a, nrb, p->stream);
@@ -591,32 +598,31 @@ cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
     a.S = p->src;
     for (int i = 0; i < 6; i++) a.sbox[i] = p->sbox[i];
   }
-  if (p->has_shell) {  // V #1: E x on the boundary layers, into the FFT buffer (steps 1-2)
-    e = run_corr_rec(p, p->x, p->K, p->state, rec, KK_CORR_X);
+  if (p->has_shell) {  // V #1: E_0 x + E_1 x on the boundary layers, into the FFT buffer (steps 1-2)
+    e = run_corr_rec(p, p->x, p->K, p->state, rec, KK_CORR_X, false);
     if (e) return e;
   }
-  e = run_transform_chain(p, a, FIRST_ITER, MID_PROP, rec);
+  e = run_transform_chain(p, a, FIRST_ITER, MID_PROP, rec);  // E_2 x inside the first pass
   if (e) return e;
-  e = run_rows_last(p, a, LAST_ITER, true, rec);
+  e = run_rows_last(p, a, LAST_ITER, true, rec, !p->has_shell);
   if (e) return e;
-  double* pshell = p->partials + p->n_rows_partials;
   if (p->has_shell) {  // V #2 on e = x - w: E e into the (now free) FFT buffer, then the layers' update
-    e = run_corr_rec(p, p->ebuf, p->K, p->state, rec, KK_CORR_E);
+    e = run_corr_rec(p, p->ebuf, p->K, p->state, rec, KK_CORR_E, true);
     if (e) return e;
     ShellArgs s = shell_args(p);
     s.state = p->state;
     s.mode = SHELL_UPDATE_ITER;
-    s.partials = pshell;
+    s.partials = p->partials;
+    s.slot0 = p->n_rows_partials;
+    s.n_total = p->n_rows_partials + kShellBlocks;
+    s.fin = p->state;
+    s.hist = p->history;
     if (rec) rec->begin(KK_SHELL_UPDATE);
     e = launch_shell(s, kShellBlocks, p->stream);
     if (rec) rec->end();
     if (e) return e;
   }
-  if (rec) rec->begin(KK_FINALIZE);
-  e = launch_finalize(p->state, p->partials, p->n_rows_partials, pshell, p->has_shell ? kShellBlocks : 0, p->history,
-                      p->stream);
-  if (rec) rec->end();
-  return e;
+  return cudaSuccess;
 }
 
 mbs_status ensure_graph(mbs_plan* p) {
@@ -833,7 +839,7 @@ mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* o
         a.S = p->src;
         for (int i = 0; i < 6; i++) a.sbox[i] = p->sbox[i];
       }
-      if (p->has_shell) e = run_corr(p, xd, p->K, p->free_state);
+      if (p->has_shell) e = run_corr(p, xd, p->K, p->free_state, false);
       if (!e) e = run_transform_chain(p, a, FIRST_ITER, MID_PROP, nullptr);
       if (!e) e = run_rows_last(p, a, LAST_PRECOND, false, nullptr);
       if (!e && p->has_shell) {
@@ -1014,8 +1020,8 @@ mbs_status mbs_solve(mbs_plan* p, const void* source, void* out, double tol, int
 }
 
 const char* mbs_kernel_kind_name(int32_t kind) {
-  static const char* names[MBS_KERNEL_KINDS] = {"corr_x",    "rows_first", "strided_fwd",  "mid_axis0", "strided_inv",
-                                                "rows_last", "corr_e",     "shell_update", "finalize"};
+  static const char* names[MBS_KERNEL_KINDS] = {"corr_x",    "rows_first", "strided_fwd", "mid_axis0",
+                                                "strided_inv", "rows_last", "corr_e",      "shell_update"};
   return (kind >= 0 && kind < MBS_KERNEL_KINDS) ? names[kind] : "";
 }
 

@@ -3,6 +3,7 @@
 
 #include "mbs_fft.cuh"
 #include "mbs_internal.h"
+#include "mbs_reduce.cuh"
 #include "../../include/mbs.h"
 
 namespace mbs {
@@ -203,18 +204,6 @@ cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st) {
   }
 }
 
-__device__ __forceinline__ double block_sum_all(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < nw; i++) s += red[i];
-  return s;
-}
-
 // Boundary-layer voxels: one warp per grid row (i0, i1); a row inside an
 // axis-0/1 layer is processed whole, other rows only at the axis-2 layers.
 // With E = C[v] (the summed corrections of the voxel), per mode:
@@ -277,58 +266,13 @@ __global__ void __launch_bounds__(256) k_shell(const __grid_constant__ ShellArgs
     }
   }
   if (a.partials) {
-    const double s = block_sum_all(acc, red);
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
+    const double s = block_sum(acc, red);
+    finish_block(Finish{a.partials, a.slot0, a.n_total, a.fin, a.hist}, s, red);
   }
 }
 
 cudaError_t launch_shell(const ShellArgs& a, int blocks, cudaStream_t st) {
   k_shell<<<blocks, 256, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
-// Deterministic FP64 sum of the per-block partials, relative residual and stop
-// test (Sec. 3.1: eps = ||Gamma^-1 (y - A x_n)|| / ||Gamma^-1 y||, threshold).
-__global__ void __launch_bounds__(1024) k_finalize(DevState* st, const double* __restrict__ p1, int n1,
-                                                   const double* __restrict__ p2, int n2, double* hist) {
-  __shared__ double red[32];
-  if (st->done) return;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n1; i += blockDim.x) s += p1[i];
-  for (int i = threadIdx.x; i < n2; i += blockDim.x) s += p2[i];
-  const double R = block_sum_all(s, red);
-  if (threadIdx.x == 0) {
-    const int it = st->iter;
-    if (it == 0) st->R0 = R;
-    const double eps = st->R0 > 0.0 ? sqrt(R / st->R0) : 0.0;
-    if (hist && it < st->hist_cap) hist[it] = eps;
-    st->eps = eps;
-    st->iter = it + 1;
-    if (!isfinite(eps) || !isfinite(R)) {
-      st->status = MBS_ENAN;
-      st->done = 1;
-    } else {
-      if (eps < st->best) {
-        st->best = eps;
-        st->rise = 0;
-      } else if (eps > 4.0 * st->best && eps > 1e-3) {
-        st->rise += 1;
-      } else {
-        st->rise = 0;
-      }
-      if (st->rise >= 20) {
-        st->status = MBS_EDIVERGE;
-        st->done = 1;
-      } else if (eps < st->tol || st->iter >= st->max_iter) {
-        st->done = 1;
-      }
-    }
-  }
-}
-
-cudaError_t launch_finalize(DevState* state, const double* p1, int n1, const double* p2, int n2, double* history,
-                            cudaStream_t st) {
-  k_finalize<<<1, 1024, 0, st>>>(state, p1, n1, p2, n2, history);
   return cudaGetLastError();
 }
 
@@ -341,6 +285,7 @@ __global__ void k_state_arm(DevState* st, int add_iter, double tol, int reset, i
     st->rise = 0;
     st->status = 0;
     st->hist_cap = hist_cap;
+    st->ticket = 0u;
   }
   st->max_iter = st->iter + add_iter;
   st->tol = tol;

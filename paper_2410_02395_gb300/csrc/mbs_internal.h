@@ -50,8 +50,9 @@ struct DevState {
   double R0;      // ||r_0||^2
   double eps;     // last relative residual
   double best;    // smallest eps so far (divergence guard)
-  int rise;       // consecutive iterations with eps > 2 * best
+  int rise;       // consecutive iterations with eps > 4 * best
   int hist_cap;
+  unsigned int ticket;  // blocks of the iteration's last kernel that have stored their partial
 };
 
 enum FirstMode { FIRST_PLAIN = 0, FIRST_ITER = 1 };
@@ -71,10 +72,15 @@ struct PassArgs {
   float2 c;             // c
   float2 ck0;           // c * k0^2
   float alpha;
+  const float2* cW;     // c * W (t x t) for the axis-2 corrections fused into the first pass
   const float2* tw;     // twiddles exp(-2 pi i k / N), k < N
   AxisTables tb;
   GridDesc g;
-  double* partials;     // per-block FP64 partial sums of |r|^2
+  double* partials;     // per-block FP64 partial sums of |r|^2 (null: none)
+  int slot0;            // this launch's first slot in partials
+  int n_total;          // partials of the whole iteration
+  DevState* fin;        // non-null: this launch ends the iteration (sum + stop test)
+  double* hist;
   const DevState* state;
   int mode;
   int nsub;             // subdomains (along the pass axis) of this size
@@ -105,6 +111,10 @@ struct ShellArgs {
   AxisTables tb;
   GridDesc g;
   double* partials;
+  int slot0;
+  int n_total;
+  DevState* fin;
+  double* hist;
   const DevState* state;
   int mode;
 };
@@ -119,8 +129,6 @@ bool fft_size_compiled(int n);
 cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st);
 bool corr_t_supported(int t);
 cudaError_t launch_shell(const ShellArgs& a, int blocks, cudaStream_t st);
-cudaError_t launch_finalize(DevState* state, const double* p1, int n1, const double* p2, int n2, double* history,
-                            cudaStream_t st);
 cudaError_t launch_state_arm(DevState* state, int add_iter, double tol, int reset, int hist_cap, cudaStream_t st);
 
 // Plan set-up kernels (FP64 arithmetic on the device).

@@ -18,21 +18,17 @@
 #pragma once
 #include "mbs_fft.cuh"
 #include "mbs_internal.h"
+#include "mbs_reduce.cuh"
 
 namespace mbs {
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < nw; i++) s += red[i];
-  }
-  return s;
+// Asynchronous 8-byte global -> shared copies (completed by cp_async_wait_all).
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Resident CTAs per SM asked of the register allocator: 32 warps per SM, i.e.
 // at most 64 registers per thread (the tiles of that many CTAs fit in 228 KB).
@@ -104,6 +100,34 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
   const float2* __restrict__ X = a.X;
   const float2* __restrict__ B = a.B;
   float2* K = a.K;
+  // Axis-2 edge corrections of x on this segment (Sec. 3.1 steps 1-5) need the
+  // segment's own first/last t voxels and the neighbours' adjacent t voxels of
+  // every row: fetched asynchronously into shared memory while the tile loads.
+  const bool e2 = iter && a.g.ax[2].a > 0;
+  const int t = a.g.t;
+  const AxisDesc& ax2 = a.g.ax[2];
+  const int L = ax2.left[j2], R = ax2.right[j2];
+  float2* xe = dyn + N * kPad;         // [32 rows][4t]: own first t, own last t, left's last t, right's first t
+  float2* wsm = xe + 32 * 4 * t;       // Toeplitz weights cw[m] = cW at column - row = m - (t - 1)
+  if (e2) {
+    for (int idx = tid; idx < 32 * 4 * t; idx += NT) {
+      const int r = idx / (4 * t), k = idx - r * 4 * t;
+      long long pos = -1;
+      if (ri[r].flags & 1) {
+        if (k < t) pos = off2 + k;
+        else if (k < 2 * t) pos = off2 + N - t + (k - t);
+        else if (k < 3 * t) pos = L >= 0 ? ax2.off[L] + ax2.n[L] - t + (k - 2 * t) : -1;
+        else pos = R >= 0 ? ax2.off[R] + (k - 3 * t) : -1;
+      }
+      if (pos >= 0) cp_async8(xe + idx, X + (ri[r].base - off2) + pos);
+      else xe[idx] = make_float2(0.f, 0.f);
+    }
+    cp_async_commit();
+    if (tid < 2 * t - 1) {
+      const int m = tid, aa = m < t - 1 ? t - 1 - m : 0, bb = aa + m - (t - 1);
+      wsm[m] = a.cW[aa * t + bb];
+    }
+  }
   for (int k0 = 0; k0 < PERT; k0 += CH) {
     float2 xv[CH], bv[CH], cv[CH];
 #pragma unroll
@@ -118,7 +142,7 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
           xv[c] = __ldg(X + gi);
           if (iter) {
             bv[c] = __ldg(B + gi);
-            if ((f & 2) || in_layer2<N>(a, e)) cv[c] = K[gi];  // E x on the boundary layers
+            if (f & 2) cv[c] = K[gi];  // E_0 x + E_1 x on the axis-0/1 boundary layers
           }
         }
       }
@@ -137,6 +161,27 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
         }
         sm[e][r] = u;
       }
+    }
+  }
+  if (e2) {
+    //   first t: u -= sum_b cW[b][q]  (x_left[n_l-t+b] - x[n-t+b])
+    //   last t:  u -= sum_b cW[aa][b] (x_right[b]      - x[b])
+    cp_async_wait_all();
+    __syncthreads();
+    for (int idx = tid; idx < 32 * 2 * t; idx += NT) {
+      const int r = idx / (2 * t), k = idx - r * 2 * t;
+      const int q = k < t ? k : N - t + (k - t);
+      if (k >= t && q < t) continue;  // also in the first range (N < 2t): done there
+      const float2* x4 = xe + r * 4 * t;
+      float2 v = make_float2(0.f, 0.f);
+      if (q < t) {
+        for (int b = 0; b < t; b++) v = cadd(v, cmul(wsm[q - b + t - 1], csub(x4[2 * t + b], x4[t + b])));
+      }
+      if (q >= N - t) {
+        const int aa = q - (N - t);
+        for (int b = 0; b < t; b++) v = cadd(v, cmul(wsm[b - aa + t - 1], csub(x4[3 * t + b], x4[b])));
+      }
+      sm[q][r] = csub(sm[q][r], v);
     }
   }
   if constexpr (N > 1) {
@@ -256,7 +301,7 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
   }
   if (a.partials) {
     const double s = block_sum((double)acc, red);
-    if (tid == 0) a.partials[blockIdx.x + (long long)gridDim.x * blockIdx.y] = s;
+    finish_block(Finish{a.partials, a.slot0, a.n_total, a.fin, a.hist}, s, red);
   }
 }
 
@@ -408,9 +453,11 @@ cudaError_t run_size(int kind, int axis, bool inv, const PassArgs& a, int nrow_b
   const unsigned gx = (unsigned)((a.g.N2 + 31) / 32);
   switch (kind) {
     case 0: {
-      e = set_smem(k_rows_first<N>, sm);
+      // tile, then the axis-2 edge values [32][4t] and the 2t-1 Toeplitz weights
+      const size_t edge = a.g.ax[2].a > 0 ? ((size_t)32 * 4 * a.g.t + 2 * a.g.t) * sizeof(float2) : 0;
+      e = set_smem(k_rows_first<N>, sm + ((size_t)32 * 4 * kMaxT + 2 * kMaxT) * sizeof(float2));
       if (e) return e;
-      k_rows_first<N><<<dim3(nrow_blocks, a.nsub), blk, sm, st>>>(a);
+      k_rows_first<N><<<dim3(nrow_blocks, a.nsub), blk, sm + edge, st>>>(a);
       break;
     }
     case 1: {
