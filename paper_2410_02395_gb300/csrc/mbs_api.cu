@@ -127,7 +127,7 @@ struct mbs_plan {
   float2* tmp_in;
   float2* tmp_out;
   float *p2[3], *invn[3];
-  int *sub[3], *loc[3], *sh2list;
+  int *sub[3], *loc[3], *sh2list, *lc[2];  // lc[d]: axis-d indices inside the layers, then outside
   float2* ebuf;  // e = x - w on the boundary layers
   unsigned char* shell[3];
   int nsh2;
@@ -197,6 +197,8 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
     psh[d] = take(p->N[d]);
   }
   char* psh2 = take(p->N[2] * sizeof(int));
+  char* plc0 = take(p->N[0] * sizeof(int));
+  char* plc1 = take(p->N[1] * sizeof(int));
   char* pcw = take(std::max(1, p->t * p->t) * sizeof(float2));
   std::map<int, char*> ptw;
   for (int d = 0; d < 3; d++)
@@ -225,6 +227,8 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
     }
     p->ebuf = (float2*)pe;
     p->sh2list = (int*)psh2;
+    p->lc[0] = (int*)plc0;
+    p->lc[1] = (int*)plc1;
     p->cW = (float2*)pcw;
     p->tw.clear();
     for (auto& kv : ptw) p->tw[kv.first] = (float2*)kv.second;
@@ -353,6 +357,17 @@ mbs_status upload_tables(mbs_plan* p) {
     CU(cudaMemcpyAsync(p->loc[d], loc.data(), N * sizeof(int), cudaMemcpyHostToDevice, p->stream));
     CU(cudaMemcpyAsync(p->shell[d], sh.data(), N, cudaMemcpyHostToDevice, p->stream));
     CU(cudaStreamSynchronize(p->stream));
+    if (d < 2) {  // indices inside the layers first, then the others
+      std::vector<int> lc;
+      for (int i = 0; i < N; i++)
+        if (sh[i]) lc.push_back(i);
+      const int nl = (int)lc.size();
+      for (int i = 0; i < N; i++)
+        if (!sh[i]) lc.push_back(i);
+      CU(cudaMemcpyAsync(p->lc[d], lc.data(), N * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+      CU(cudaStreamSynchronize(p->stream));
+      if (d == 0) p->tb.nl0 = nl; else p->tb.nl1 = nl;
+    }
     if (d == 2) {
       std::vector<int> list;
       for (int i = 0; i < N; i++)
@@ -383,6 +398,10 @@ mbs_status upload_tables(mbs_plan* p) {
   }
   tb.sh2list = p->sh2list;
   tb.nsh2 = p->nsh2;
+  tb.l0 = p->lc[0];
+  tb.c0 = p->lc[0] + tb.nl0;
+  tb.l1 = p->lc[1];
+  tb.c1 = p->lc[1] + tb.nl1;
   return MBS_OK;
 }
 

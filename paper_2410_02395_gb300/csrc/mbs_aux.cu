@@ -103,6 +103,59 @@ __global__ void __launch_bounds__(128) k_corr_strided(const __grid_constant__ Co
   for (int q = 0; q < T; q++) put(C, base + (long long)(off + q) * stride, outf[q], add);
 }
 
+// Axes 0 and 1 when every subdomain on the axis has n >= 2t (the first and last
+// layer ranges do not overlap): one thread per (pencil, subdomain, side), so
+// each thread holds only t inputs (twice the threads, half the registers).
+//   side 0 (first t):  out[q]        = sum_b w[q - b + t - 1] (f_left[n_l-t+b] - f_s[n-t+b])
+//   side 1 (last t):   out[n-t+aa]   = sum_b w[b - aa + t - 1] (f_right[b]      - f_s[b])
+template <int T>
+__global__ void __launch_bounds__(128) k_corr_side(const __grid_constant__ CorrArgs a) {
+  if (a.state && a.state->done) return;
+  const int d = a.axis;
+  const AxisDesc& ax = a.g.ax[d];
+  const long long N0 = a.g.N0, N1 = a.g.N1, N2 = a.g.N2;
+  const long long npen = d == 0 ? N1 * N2 : N0 * N2;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= 2 * npen * ax.S) return;
+  const int ss = (int)(gid / npen);  // subdomain * 2 + side
+  const int s = ss >> 1, side = ss & 1;
+  const long long p = gid - (long long)ss * npen;
+  long long base, stride;
+  bool add = false;
+  if (d == 0) {
+    base = p;
+    stride = N1 * N2;
+  } else {
+    const long long i0 = p / N2, i2 = p - i0 * N2;
+    base = i0 * N1 * N2 + i2;
+    stride = N2;
+    add = a.tb.shell[0][i0];
+  }
+  const int off = ax.off[s], n = ax.n[s];
+  const int nb = side ? ax.right[s] : ax.left[s];
+  const long long own0 = base + (long long)(side ? off : off + n - T) * stride;
+  const long long nb0 = nb >= 0 ? base + (long long)(side ? ax.off[nb] : ax.off[nb] + ax.n[nb] - T) * stride : 0;
+  const float2* __restrict__ F = a.F;
+  float2 G[T];
+#pragma unroll
+  for (int b = 0; b < T; b++) {
+    const float2 o = F[own0 + (long long)b * stride];
+    const float2 v = nb >= 0 ? F[nb0 + (long long)b * stride] : make_float2(0.f, 0.f);
+    G[b] = csub(v, o);
+  }
+  float2 w[2 * T - 1];
+  load_toeplitz<T>(a.cW, w);
+  float2* C = a.C;
+  const long long out0 = base + (long long)(side ? off + n - T : off) * stride;
+#pragma unroll
+  for (int q = 0; q < T; q++) {
+    float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < T; b++) v = cadd(v, cmul(side ? w[b - q + T - 1] : w[q - b + T - 1], G[b]));
+    put(C, out0 + (long long)q * stride, v, add);
+  }
+}
+
 // Axis 2: one warp per grid row; the row's 2t layer values of every subdomain
 // are staged in shared memory with coalesced loads, then each lane produces
 // outputs from shared memory.
@@ -183,8 +236,15 @@ cudaError_t launch_corr_t(const CorrArgs& a, cudaStream_t st) {
     return cudaGetLastError();
   }
   const long long npen = a.axis == 0 ? a.g.N1 * a.g.N2 : a.g.N0 * a.g.N2;
-  const unsigned blocks = (unsigned)((npen * ax.S + 127) / 128);
-  k_corr_strided<T><<<blocks, 128, 0, st>>>(a);
+  bool split = true;
+  for (int s = 0; s < ax.S; s++) split = split && ax.n[s] >= 2 * T;
+  if (split) {
+    const unsigned blocks = (unsigned)((2 * npen * ax.S + 127) / 128);
+    k_corr_side<T><<<blocks, 128, 0, st>>>(a);
+  } else {
+    const unsigned blocks = (unsigned)((npen * ax.S + 127) / 128);
+    k_corr_strided<T><<<blocks, 128, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -204,66 +264,98 @@ cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st) {
   }
 }
 
-// Boundary-layer voxels: one warp per grid row (i0, i1); a row inside an
-// axis-0/1 layer is processed whole, other rows only at the axis-2 layers.
-// With E = C[v] (the summed corrections of the voxel), per mode:
+// Boundary-layer voxels, with E = C[v] (the summed corrections of the voxel):
 //   UPDATE_ITER:    r = B e - E, x <- x - alpha r, FP64 |r|^2   (e from the last pass)
 //   UPDATE_PRECOND: out = -(B e - E)
 //   ADD_E:          out += E          SET_E: out = E
-// Each lane handles up to 4 voxels of a row per round with all loads issued first.
+// Two index spaces, both walked in batches of U voxels per thread with every
+// load issued first: (1) whole grid rows inside an axis-0/1 layer (warp per
+// row), (2) the axis-2 layer positions of all other rows, flattened.
+template <int U>
+__device__ __forceinline__ float shell_batch(const ShellArgs& a, const long long (&v)[U]) {
+  const int mode = a.mode;
+  const bool upd = mode == SHELL_UPDATE_ITER || mode == SHELL_UPDATE_PRECOND;
+  float2 ev[U], cv[U], xv[U], bv[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    if (v[u] < 0) continue;
+    cv[u] = a.C[v[u]];
+    if (upd) {
+      ev[u] = a.E[v[u]];
+      bv[u] = a.B[v[u]];
+      if (mode == SHELL_UPDATE_ITER) xv[u] = a.X[v[u]];
+    } else if (mode == SHELL_ADD_E) {
+      xv[u] = a.out[v[u]];
+    }
+  }
+  float racc = 0.f;
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    if (v[u] < 0) continue;
+    if (upd) {
+      const float2 r = csub(cmul(bv[u], ev[u]), cv[u]);
+      racc = fmaf(r.x, r.x, fmaf(r.y, r.y, racc));
+      if (mode == SHELL_UPDATE_ITER)
+        a.X[v[u]] = make_float2(fmaf(-a.alpha, r.x, xv[u].x), fmaf(-a.alpha, r.y, xv[u].y));
+      else
+        a.out[v[u]] = make_float2(-r.x, -r.y);
+    } else if (mode == SHELL_ADD_E) {
+      a.out[v[u]] = cadd(xv[u], cv[u]);
+    } else {
+      a.out[v[u]] = cv[u];
+    }
+  }
+  return racc;
+}
+
 __global__ void __launch_bounds__(256) k_shell(const __grid_constant__ ShellArgs a) {
   __shared__ double red[8];
   if (a.state && a.state->done) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long N1 = a.g.N1, N2 = a.g.N2;
-  const long long rows = a.g.N0 * N1;
-  const int mode = a.mode;
-  const bool upd = mode == SHELL_UPDATE_ITER || mode == SHELL_UPDATE_PRECOND;
   constexpr int U = 4;
-  double acc = 0.0;  // FP64 across rounds; each round's (<= U voxels) partial is FP32
-  for (long long rho = (long long)blockIdx.x * 8 + warp; rho < rows; rho += (long long)gridDim.x * 8) {
-    const long long i0 = rho / N1, i1 = rho - i0 * N1;
-    const bool full = a.tb.shell[0][i0] || a.tb.shell[1][i1];
-    const long long cnt = full ? N2 : a.tb.nsh2;
-    for (long long k0 = 0; k0 < cnt; k0 += 32 * U) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long N2 = a.g.N2;
+  double acc = 0.0;  // FP64 across batches; each batch's (<= U voxels) partial is FP32
+  // (1) rows inside an axis-0/1 layer: warp per row
+  const long long nfull = (long long)a.tb.nl0 * a.g.N1 + (long long)(a.g.N0 - a.tb.nl0) * a.tb.nl1;
+  for (long long fr = (long long)blockIdx.x * 8 + warp; fr < nfull; fr += (long long)gridDim.x * 8) {
+    long long i0, i1;
+    const long long f0 = (long long)a.tb.nl0 * a.g.N1;
+    if (fr < f0) {  // i0 in an axis-0 layer, any i1
+      i0 = a.tb.l0[fr / a.g.N1];
+      i1 = fr - (fr / a.g.N1) * a.g.N1;
+    } else {        // i0 outside, i1 in an axis-1 layer
+      const long long q = fr - f0;
+      i0 = a.tb.c0[q / a.tb.nl1];
+      i1 = a.tb.l1[q - (q / a.tb.nl1) * a.tb.nl1];
+    }
+    const long long rb = (i0 * a.g.N1 + i1) * N2;
+    for (long long k0 = 0; k0 < N2; k0 += 32 * U) {
       long long v[U];
-      float2 ev[U], cv[U], xv[U], bv[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const long long k = k0 + lane + 32 * u;
-        v[u] = -1;
-        if (k < cnt) {
-          const long long i2 = full ? k : a.tb.sh2list[k];
-          v[u] = rho * N2 + i2;
-          cv[u] = a.C[v[u]];
-          if (upd) {
-            ev[u] = a.E[v[u]];
-            bv[u] = a.B[v[u]];
-            if (mode == SHELL_UPDATE_ITER) xv[u] = a.X[v[u]];
-          } else if (mode == SHELL_ADD_E) {
-            xv[u] = a.out[v[u]];
-          }
-        }
+        v[u] = k < N2 ? rb + k : -1;
       }
-      float racc = 0.f;
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        if (v[u] < 0) continue;
-        if (upd) {
-          const float2 r = csub(cmul(bv[u], ev[u]), cv[u]);
-          racc = fmaf(r.x, r.x, fmaf(r.y, r.y, racc));
-          if (mode == SHELL_UPDATE_ITER)
-            a.X[v[u]] = make_float2(fmaf(-a.alpha, r.x, xv[u].x), fmaf(-a.alpha, r.y, xv[u].y));
-          else
-            a.out[v[u]] = make_float2(-r.x, -r.y);
-        } else if (mode == SHELL_ADD_E) {
-          a.out[v[u]] = cadd(xv[u], cv[u]);
-        } else {
-          a.out[v[u]] = cv[u];
-        }
-      }
-      acc += (double)racc;
+      acc += (double)shell_batch<U>(a, v);
     }
+  }
+  // (2) axis-2 layer positions of rows outside the axis-0/1 layers, flattened
+  const long long nc1 = a.g.N1 - a.tb.nl1;
+  const long long npart = (a.g.N0 - a.tb.nl0) * nc1 * a.tb.nsh2;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; j0 < npart; j0 += nth * U) {
+    long long v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const long long j = j0 + nth * u;
+      v[u] = -1;
+      if (j < npart) {
+        const long long row = j / a.tb.nsh2, k = j - row * a.tb.nsh2;
+        const long long i0 = a.tb.c0[row / nc1], i1 = a.tb.c1[row - (row / nc1) * nc1];
+        v[u] = (i0 * a.g.N1 + i1) * N2 + a.tb.sh2list[k];
+      }
+    }
+    acc += (double)shell_batch<U>(a, v);
   }
   if (a.partials) {
     const double s = block_sum(acc, red);

@@ -37,6 +37,9 @@ struct AxisTables {
   const unsigned char* shell[3];  // 1 if a_d >= 1 and the voxel lies in the first/last t layers
   const int* sh2list;     // global axis-2 indices with shell[2] set
   int nsh2;
+  // indices along axes 0 and 1 inside (l) and outside (c) the boundary layers
+  const int *l0, *c0, *l1, *c1;
+  int nl0, nl1;
 };
 
 // Device-side solver state (one per plan). Every iteration kernel leaves at once

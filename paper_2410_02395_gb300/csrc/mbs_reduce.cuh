@@ -71,10 +71,14 @@ __device__ __forceinline__ void finish_block(const Finish& f, double block_total
   __shared__ unsigned int ticket;
   const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
-  if (threadIdx.x == 0) f.partials[f.slot0 + b] = block_total;
+  if (threadIdx.x == 0) {
+    f.partials[f.slot0 + b] = block_total;
+    if (f.state) {
+      __threadfence();  // the partial is visible before the ticket is taken
+      ticket = atomicAdd(&f.state->ticket, 1u);
+    }
+  }
   if (!f.state) return;
-  __threadfence();
-  if (threadIdx.x == 0) ticket = atomicAdd(&f.state->ticket, 1u);
   __syncthreads();
   if (ticket != nb - 1) return;
   __threadfence();
