@@ -77,7 +77,10 @@ typedef enum mbs_operator {
 #define MBS_MAX_EDGE 512 /* longest subdomain edge; edges must factor into 2, 3, 5, 7 */
 
 /* Option flags. */
-#define MBS_FLAG_NO_GRAPH (1u << 0) /* launch kernels one by one instead of replaying a CUDA graph */
+#define MBS_FLAG_NO_GRAPH (1u << 0)  /* launch kernels one by one instead of replaying a CUDA graph */
+#define MBS_FLAG_CORR_TF32 (1u << 1) /* edge-correction contractions on the tensor cores as 3xTF32 with
+                                        FP32 accumulation (mma.sync m16n8k8); needs every corrected
+                                        subdomain edge >= 2t. Default: FP32 CUDA-core products.   */
 
 typedef struct mbs_options {
   int32_t truncation;        /* t, the kept edge width (Sec. 3, Fig. 5); 0 -> 8 (Sec. 3.3)      */

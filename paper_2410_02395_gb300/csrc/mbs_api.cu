@@ -294,6 +294,8 @@ mbs_status validate_and_fill(mbs_plan* p, const int64_t shape[3], double h, doub
         return fail(MBS_EUNSUPPORTED, "subdomain edge " + std::to_string(n) +
                                           " is not a compiled FFT length (2^a 3^b 5^c 7^d list, <= 512)");
       if (p->a[d] > 0 && p->t > n) return fail(MBS_EINVAL, "truncation t exceeds a subdomain edge");
+      if ((p->flags & MBS_FLAG_CORR_TF32) && p->a[d] > 0 && 2 * p->t > n)
+        return fail(MBS_EUNSUPPORTED, "tensor-core corrections need subdomain edges >= 2t");
     }
   }
   for (int i = 0; i < 6; i++) {
@@ -463,6 +465,7 @@ PassArgs base_args(mbs_plan* p) {
   a.mc = make_float2((float)-p->c_re, (float)-p->c_im);
   a.alpha = (float)p->alpha;
   a.cW = p->cW;
+  a.fuse_e2 = (p->flags & MBS_FLAG_CORR_TF32) ? 0 : 1;
   a.tb = p->tb;
   a.g = p->g;
   return a;
@@ -514,6 +517,9 @@ cudaError_t run_corr_rec(mbs_plan* p, const float2* F, float2* C, const DevState
   memset(&c, 0, sizeof(c));
   c.F = F;
   c.C = C;
+  c.c = make_float2((float)p->c_re, (float)p->c_im);
+  c.tc = (p->flags & MBS_FLAG_CORR_TF32) ? 1 : 0;
+  if (c.tc) axis2 = true;  // no fused axis-2 path in the tensor-core form
   c.cW = p->cW;
   c.tb = p->tb;
   c.g = p->g;

@@ -221,6 +221,148 @@ __global__ void __launch_bounds__(256) k_corr_rows(const __grid_constant__ CorrA
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core form of the edge corrections (3xTF32, FP32 accumulation).
+// c is purely imaginary and W real, so E f = c (W g) with g the real and the
+// imaginary parts of the gathered differences as separate columns. One warp
+// handles 32 pencils of one (subdomain, side): A = [64 pencil-components][TP]
+// (row 2p: real part, 2p+1: imaginary part; TP = t rounded up to 8, zero
+// padded), B[k][n] = W^T or W, D = A B with mma.sync m16n8k8 TF32 in three
+// products a_hi b_hi + a_hi b_lo + a_lo b_hi (Ootomo & Yokota's split, hi =
+// round-to-nearest TF32, lo = TF32 of the remainder), then out = c D.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned tf32_hi(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int TP>
+__global__ void __launch_bounds__(128) k_corr_tc(const __grid_constant__ CorrArgs a) {
+  __shared__ float As[4][64][TP + 4];  // per warp; +4 keeps the fragment reads conflict-free
+  __shared__ float Wr[TP][TP + 1];     // real W (not scaled by c), zero padded
+  if (a.state && a.state->done) return;
+  const int d = a.axis, t = a.g.t;
+  const AxisDesc& ax = a.g.ax[d];
+  const long long N0 = a.g.N0, N1 = a.g.N1, N2 = a.g.N2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // W from c W: c = i c_im (c_re = 0), so W = Im(cW) / c_im
+  const float cim = a.c.y;
+  for (int i = threadIdx.x; i < TP * TP; i += blockDim.x) {
+    const int r = i / TP, q = i - r * TP;
+    Wr[r][q] = (r < t && q < t) ? a.cW[r * t + q].y / cim : 0.f;
+  }
+  __syncthreads();
+  const long long npen = d == 0 ? N1 * N2 : (d == 1 ? N0 * N2 : N0 * N1);
+  const long long ngroups = (npen + 31) / 32;
+  const long long wid = (long long)blockIdx.x * 4 + warp;  // (group, subdomain, side)
+  if (wid >= ngroups * ax.S * 2) return;
+  const int ss = (int)(wid / ngroups);
+  const int s = ss >> 1, side = ss & 1;
+  const long long p = (wid - (long long)ss * ngroups) * 32 + lane;
+  const bool valid = p < npen;
+  long long base = 0, stride;
+  bool add = false;
+  if (d == 0) {
+    base = p;
+    stride = N1 * N2;
+  } else if (d == 1) {
+    const long long i0 = p / N2, i2 = p - i0 * N2;
+    base = i0 * N1 * N2 + i2;
+    stride = N2;
+    if (valid) add = a.tb.shell[0][i0];
+  } else {
+    const long long i0 = p / N1, i1 = p - i0 * N1;
+    base = p * N2;
+    stride = 1;
+    if (valid) add = a.tb.shell[0][i0] || a.tb.shell[1][i1];
+  }
+  const int off = ax.off[s], n = ax.n[s];
+  const int nb = side ? ax.right[s] : ax.left[s];
+  const long long own0 = base + (long long)(side ? off : off + n - t) * stride;
+  const long long nb0 = nb >= 0 ? base + (long long)(side ? ax.off[nb] : ax.off[nb] + ax.n[nb] - t) * stride : 0;
+  // gather g = f_neighbour - f_own into the warp's A rows 2*lane, 2*lane+1
+  for (int b = 0; b < TP; b++) {
+    float2 g = make_float2(0.f, 0.f);
+    if (valid && b < t) {
+      const float2 o = a.F[own0 + (long long)b * stride];
+      const float2 v = nb >= 0 ? a.F[nb0 + (long long)b * stride] : make_float2(0.f, 0.f);
+      g = csub(v, o);
+    }
+    As[warp][2 * lane][b] = g.x;
+    As[warp][2 * lane + 1][b] = g.y;
+  }
+  __syncwarp();
+  const int gq = lane >> 2, tg = lane & 3;
+  float D[4][TP / 8][4];  // [m-tile][n-tile][fragment]
+#pragma unroll
+  for (int mt = 0; mt < 4; mt++)
+#pragma unroll
+    for (int nt = 0; nt < TP / 8; nt++)
+#pragma unroll
+      for (int i = 0; i < 4; i++) D[mt][nt][i] = 0.f;
+#pragma unroll
+  for (int ks = 0; ks < TP / 8; ks++) {
+    // B fragments: side 0 (first t): out[q] = sum_b W[b][q] g[b]  -> B[k=b][n=q] = W[b][q]
+    //              side 1 (last t):  out[q] = sum_b W[q][b] g[b]  -> B[k=b][n=q] = W[q][b]
+    unsigned bh[TP / 8][2], bl[TP / 8][2];
+#pragma unroll
+    for (int nt = 0; nt < TP / 8; nt++) {
+#pragma unroll
+      for (int j = 0; j < 2; j++) {
+        const int k = ks * 8 + tg + 4 * j, q = nt * 8 + gq;
+        const float w = side ? Wr[q][k] : Wr[k][q];
+        bh[nt][j] = tf32_hi(w);
+        bl[nt][j] = tf32_hi(w - __uint_as_float(bh[nt][j]));
+      }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 4; mt++) {
+      unsigned ah[4], al[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const int r = mt * 16 + gq + 8 * (i & 1), k = ks * 8 + tg + 4 * (i >> 1);
+        const float v = As[warp][r][k];
+        ah[i] = tf32_hi(v);
+        al[i] = tf32_hi(v - __uint_as_float(ah[i]));
+      }
+#pragma unroll
+      for (int nt = 0; nt < TP / 8; nt++) {
+        mma_tf32(D[mt][nt], al, bh[nt]);
+        mma_tf32(D[mt][nt], ah, bl[nt]);
+        mma_tf32(D[mt][nt], ah, bh[nt]);
+      }
+    }
+  }
+  __syncwarp();
+  // D fragments back to the warp's rows (A is no longer needed)
+#pragma unroll
+  for (int mt = 0; mt < 4; mt++)
+#pragma unroll
+    for (int nt = 0; nt < TP / 8; nt++)
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const int r = mt * 16 + gq + 8 * (i >> 1), q = nt * 8 + 2 * tg + (i & 1);
+        As[warp][r][q] = D[mt][nt][i];
+      }
+  __syncwarp();
+  if (!valid) return;
+  const float2 c = a.c;
+  const long long out0 = base + (long long)(side ? off + n - t : off) * stride;
+  for (int q = 0; q < t; q++) {
+    const float2 v = cmul(c, make_float2(As[warp][2 * lane][q], As[warp][2 * lane + 1][q]));
+    put(a.C, out0 + (long long)q * stride, v, add);
+  }
+}
+
 template <int T>
 cudaError_t launch_corr_t(const CorrArgs& a, cudaStream_t st) {
   const AxisDesc& ax = a.g.ax[a.axis];
@@ -250,7 +392,30 @@ cudaError_t launch_corr_t(const CorrArgs& a, cudaStream_t st) {
 
 bool corr_t_supported(int t) { return (t >= 1 && t <= 16) || t == 20 || t == 24 || t == 32; }
 
+cudaError_t launch_corr_tc(const CorrArgs& a, cudaStream_t st) {
+  const AxisDesc& ax = a.g.ax[a.axis];
+  const long long npen = a.axis == 0 ? a.g.N1 * a.g.N2 : (a.axis == 1 ? a.g.N0 * a.g.N2 : a.g.N0 * a.g.N1);
+  const long long warps = (npen + 31) / 32 * ax.S * 2;
+  const unsigned blocks = (unsigned)((warps + 3) / 4);
+  const int t = a.g.t;
+  if (t <= 8)
+    k_corr_tc<8><<<blocks, 128, 0, st>>>(a);
+  else if (t <= 16)
+    k_corr_tc<16><<<blocks, 128, 0, st>>>(a);
+  else if (t <= 24)
+    k_corr_tc<24><<<blocks, 128, 0, st>>>(a);
+  else
+    k_corr_tc<32><<<blocks, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st) {
+  if (a.tc) {
+    // the two ranges must not overlap (every subdomain on the axis has n >= 2t)
+    for (int s = 0; s < a.g.ax[a.axis].S; s++)
+      if (a.g.ax[a.axis].n[s] < 2 * a.g.t) return cudaErrorInvalidValue;
+    return launch_corr_tc(a, st);
+  }
   switch (a.g.t) {
 #define MBS_T(T) \
   case T:        \

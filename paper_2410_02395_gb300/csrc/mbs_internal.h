@@ -76,6 +76,7 @@ struct PassArgs {
   float2 ck0;           // c * k0^2
   float alpha;
   const float2* cW;     // c * W (t x t) for the axis-2 corrections fused into the first pass
+  int fuse_e2;          // 1: the first pass computes E_2 x itself; 0: E_2 x is in K with E_0 x, E_1 x
   const float2* tw;     // twiddles exp(-2 pi i k / N), k < N
   AxisTables tb;
   GridDesc g;
@@ -97,6 +98,8 @@ struct CorrArgs {
   const float2* F;      // field the corrections are taken of
   float2* C;            // correction buffer (only boundary-layer voxels are written)
   const float2* cW;     // c * W, t x t, row-major
+  float2 c;             // c (purely imaginary, Eq. c_scale2)
+  int tc;               // 1: 3xTF32 tensor-core products, 0: FP32 CUDA cores
   AxisTables tb;
   GridDesc g;
   const DevState* state;

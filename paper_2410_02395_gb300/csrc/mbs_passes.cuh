@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
   // Axis-2 edge corrections of x on this segment (Sec. 3.1 steps 1-5) need the
   // segment's own first/last t voxels and the neighbours' adjacent t voxels of
   // every row: fetched asynchronously into shared memory while the tile loads.
-  const bool e2 = iter && a.g.ax[2].a > 0;
+  const bool e2 = iter && a.fuse_e2 && a.g.ax[2].a > 0;
   const int t = a.g.t;
   const AxisDesc& ax2 = a.g.ax[2];
   const int L = ax2.left[j2], R = ax2.right[j2];
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
           xv[c] = __ldg(X + gi);
           if (iter) {
             bv[c] = __ldg(B + gi);
-            if (f & 2) cv[c] = K[gi];  // E_0 x + E_1 x on the axis-0/1 boundary layers
+            if ((f & 2) || (!a.fuse_e2 && in_layer2<N>(a, e))) cv[c] = K[gi];  // E x computed by the correction kernels
           }
         }
       }

@@ -1,0 +1,118 @@
+"""Full-size parity on the benchmark workloads, in the launch configuration the
+benchmark times (CUDA-graph replays, default plan options).
+
+Where the oracle is affordable it runs the same steps (the C1 64^3 workload
+for tens of iterations; one preconditioned-residual evaluation and one
+iteration of the 256^3 C2 workload); otherwise properties that hold at any
+size are checked: eps_0 = 1, a monotone residual, and graph replays equal to
+kernel-by-kernel launches bit for bit.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import Problem, relative_l2  # noqa: E402
+from synth import config_problem  # noqa: E402
+
+ITER_TOL = 1e-4
+OP_TOL = 1e-5
+
+
+def _plan(params, n, **kw):
+    import paper_2410_02395_gb300 as pkg
+
+    return pkg.Plan(params["shape"], params["pixel"], params["wavelength"], torch.from_numpy(n).cuda(),
+                    boundary_widths=params["widths"], split=params["split"], truncation=params["t"],
+                    periodic=params["periodic"], **kw)
+
+
+def _oracle(params, n):
+    return Problem(n, params["pixel"], params["wavelength"], widths=params["widths"], split=params["split"],
+                   periodic=params["periodic"], t=params["t"])
+
+
+@pytest.fixture(scope="module")
+def c1():
+    params, n, src = config_problem("C1")
+    plan = _plan(params, n)
+    yield params, n, src, plan
+    plan.close()
+
+
+@pytest.fixture(scope="module")
+def c2():
+    params, n, src = config_problem("C2")
+    plan = _plan(params, n)
+    yield params, n, src, plan
+    plan.close()
+
+
+def test_c1_iterations_match_oracle(c1):
+    params, n, src, plan = c1
+    n_iter = 2 * plan.info()["graph_iters"]      # two whole graph replays
+    plan.set_source(torch.from_numpy(src).cuda())
+    st, it, eps = plan.iterate(n_iter, 0.0, no_poll=True)
+    x = plan.field(like=torch.zeros(1, device="cuda"))
+    xr, itr, histr = _oracle(params, n).solve(src, tol=0.0, max_iter=n_iter)
+    assert it == itr == n_iter
+    assert relative_l2(x.cpu().numpy(), xr) < ITER_TOL
+    np.testing.assert_allclose(plan.history(n_iter), histr, rtol=1e-4, atol=1e-6)
+
+
+def test_c1_solve_to_tolerance(c1):
+    """The C1 workload's own stopping threshold (1e-5): iteration count and field."""
+    params, n, src, plan = c1
+    x, it, res = plan.solve(torch.from_numpy(src).cuda(), tol=params["tol"], max_iter=5000)
+    xr, itr, _ = _oracle(params, n).solve(src, tol=params["tol"], max_iter=5000)
+    assert res < params["tol"]
+    assert abs(it - itr) <= 2
+    assert relative_l2(x.cpu().numpy(), xr) < 1e-4
+
+
+def test_c2_preconditioned_residual_matches_oracle(c2):
+    """a1-a6 on the full 256^3, 2x2x2 workload: Gamma^-1 y at x = 0 (the first residual)."""
+    params, n, src, plan = c2
+    plan.set_source(torch.from_numpy(src).cuda())
+    got = plan.apply("PRECOND", torch.zeros(params["shape"], dtype=torch.complex64, device="cuda"))
+    ref = _oracle(params, n)
+    want = ref.preconditioned_residual(np.zeros(params["shape"]), ref.scaled_source(src))
+    assert relative_l2(got.cpu().numpy(), want) < OP_TOL
+
+
+def test_c2_first_iterations_match_oracle(c2):
+    params, n, src, plan = c2
+    plan.set_source(torch.from_numpy(src).cuda())
+    st, it, eps = plan.iterate(2, 0.0)
+    x = plan.field(like=torch.zeros(1, device="cuda"))
+    xr, itr, histr = _oracle(params, n).solve(src, tol=0.0, max_iter=2)
+    assert it == itr == 2
+    assert relative_l2(x.cpu().numpy(), xr) < ITER_TOL
+    np.testing.assert_allclose(plan.history(2), histr, rtol=1e-5)
+
+
+def test_c2_graph_replay_equals_direct_launches(c2):
+    """The benchmark's graph replays compute exactly what one-by-one launches compute."""
+    params, n, src, plan = c2
+    K = 3 * plan.info()["graph_iters"]
+    plan.set_source(torch.from_numpy(src).cuda())
+    plan.iterate(K, 0.0, no_poll=True)
+    xg = plan.field(like=torch.zeros(1, device="cuda"))
+    direct = _plan(params, n, no_graph=True)
+    direct.set_source(torch.from_numpy(src).cuda())
+    direct.iterate(K, 0.0)
+    xd = direct.field(like=torch.zeros(1, device="cuda"))
+    direct.close()
+    assert torch.equal(xg, xd)
+
+
+def test_c2_residual_monotone_from_one(c2):
+    """eps_0 = 1 and a non-increasing residual (Sec. 2) over 300 graph-replayed iterations."""
+    params, n, src, plan = c2
+    plan.set_source(torch.from_numpy(src).cuda())
+    plan.iterate(300, 0.0, no_poll=True)
+    h = plan.history(300)
+    assert len(h) == 300 and h[0] == 1.0
+    assert np.all(h[1:] <= h[:-1] * (1 + 1e-5))

@@ -53,9 +53,19 @@ CASES = {
 }
 
 
-@pytest.fixture(scope="module", params=sorted(CASES))
+TF32_CASES = ["cube_2x2x2", "uneven_sizes", "single_nonperiodic", "periodic_split_seam"]
+
+
+@pytest.fixture(scope="module", params=sorted(CASES) + ["tf32:" + c for c in TF32_CASES])
 def pair(request):
-    plan, ref, n = make_pair(**CASES[request.param])
+    """(plan, oracle) on one case; "tf32:" cases run the edge corrections as 3xTF32
+    tensor-core products (same tolerances: the split recovers FP32 accuracy)."""
+    name = request.param
+    kw = {}
+    if name.startswith("tf32:"):
+        name = name[5:]
+        kw["corr_tf32"] = True
+    plan, ref, n = make_pair(**CASES[name], **kw)
     yield plan, ref
     plan.close()
 
