@@ -201,6 +201,28 @@ MBS_API mbs_status mbs_profile_iterations(mbs_plan *plan, int32_t n_iter, int32_
                                   double ms[MBS_KERNEL_KINDS]);
 MBS_API const char *mbs_kernel_kind_name(int32_t kind);
 
+/*
+ * Edge corrections without allocation: out = E x, the same operator as
+ * mbs_apply_operator(plan, MBS_OP_E, x, out) (the paper has no counterpart of
+ * this entry point). It is for callers that must not trigger a device
+ * allocation when they call, for instance a process whose device memory is
+ * handed out entirely by another framework's caching allocator or by a fixed
+ * memory budget: mbs_apply_operator may allocate staging buffers on first use.
+ * Here the correction scratch is a fixed 16 MiB array inside the library (every
+ * GPU that loads the library holds it until the process exits), the plan's own
+ * buffers are not touched, and nothing is allocated on any path.
+ *  - x and out: device pointers only (complex64, the plan's grid); host pointers
+ *    are rejected with MBS_EINVAL because they would need a staging buffer.
+ *  - grids above 2^21 voxels (the scratch's capacity) are rejected with MBS_EINVAL.
+ *  - The first call on a device looks up the scratch's device address with that
+ *    device current; make that first call before any stream capture.
+ *  - All calls share the scratch: calls whose work overlaps on the GPU (on
+ *    different streams or plans) race. Runs on the plan's stream, synchronous.
+ *  - Errors: mbs_noalloc_last_error() describes the last failure of this call.
+ */
+MBS_API mbs_status mbs_apply_edge_corrections_noalloc(const mbs_plan *plan, const void *x, void *out);
+MBS_API const char *mbs_noalloc_last_error(void);
+
 MBS_API void mbs_plan_destroy(mbs_plan *plan);
 
 /* Thread-local description of the last error (empty string if none). */

@@ -687,6 +687,20 @@ mbs_status stage_in(mbs_plan* p, const void* src, float2** dev_out, float2** scr
 
 }  // namespace
 
+bool mbs_plan_corr_view(const mbs_plan* p, CorrView* v) {
+  if (!p || !v) return false;
+  v->g = p->g;
+  v->tb = p->tb;
+  v->cW = p->cW;
+  v->c = make_float2((float)p->c_re, (float)p->c_im);
+  v->tc = (p->flags & MBS_FLAG_CORR_TF32) ? 1 : 0;
+  v->has_shell = p->has_shell;
+  v->nvox = nvox(p);
+  v->free_state = p->free_state;
+  v->stream = p->stream;
+  return true;
+}
+
 extern "C" {
 
 void mbs_default_options(mbs_options* o) {

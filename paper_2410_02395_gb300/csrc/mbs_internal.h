@@ -149,4 +149,21 @@ cudaError_t launch_zero(float2* p, int64_t n, cudaStream_t st);
 cudaError_t launch_negate_copy(const float2* in, float2* out, int64_t n, cudaStream_t st);
 cudaError_t launch_pointwise_V(const float2* X, const float2* B, float2* out, int64_t n, cudaStream_t st);
 
+// Read-only view of a plan's edge-correction set-up (tables, weights, stream),
+// for entry points that bring their own scratch.
+struct CorrView {
+  GridDesc g;
+  AxisTables tb;
+  const float2* cW;
+  float2 c;
+  int tc;
+  bool has_shell;
+  int64_t nvox;
+  const DevState* free_state;
+  cudaStream_t stream;
+};
+
 }  // namespace mbs
+
+struct mbs_plan;
+bool mbs_plan_corr_view(const mbs_plan* p, mbs::CorrView* v);
