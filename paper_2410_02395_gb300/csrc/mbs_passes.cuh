@@ -16,6 +16,9 @@
 // All transforms are per subdomain: a pass along axis d launches one grid per
 // distinct subdomain size along d; grid.z (or .y) selects the subdomain.
 #pragma once
+#include <mutex>
+#include <unordered_map>
+
 #include "mbs_fft.cuh"
 #include "mbs_internal.h"
 #include "mbs_reduce.cuh"
@@ -431,17 +434,32 @@ inline size_t tile_bytes(int n) { return (size_t)n * kPad * sizeof(float2); }
 // (forward + multiplier + inverse keeps more values live than a single pass).
 constexpr int mid_min_blocks(int n) { return 24 / warps_for(n) > 1 ? 24 / warps_for(n) : 1; }
 
-// Once per kernel: the largest shared-memory carveout (several tiles per SM)
-// and, above 48 KB, the dynamic shared-memory opt-in.
+// Per kernel (keyed by its address): the largest shared-memory carveout
+// (several tiles per SM) and, above 48 KB, the dynamic shared-memory opt-in
+// for the largest size requested so far.
+struct KernelAttrs {
+  std::mutex mu;
+  std::unordered_map<const void*, size_t> smem;     // opted-in dynamic bytes
+};
+inline KernelAttrs& kernel_attrs() {
+  static KernelAttrs k;
+  return k;
+}
+
 template <class K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                       (int)cudaSharedmemCarveoutMaxShared);
+  KernelAttrs& ka = kernel_attrs();
+  std::lock_guard<std::mutex> lk(ka.mu);
+  const void* key = (const void*)kernel;
+  auto it = ka.smem.find(key);
+  if (it != ka.smem.end() && it->second >= bytes) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  if (it == ka.smem.end())
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess && bytes > 48 * 1024)
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) done = true;
+  if (e == cudaSuccess) ka.smem[key] = bytes;
   return e;
 }
 
