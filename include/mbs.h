@@ -81,6 +81,12 @@ typedef enum mbs_operator {
 #define MBS_FLAG_CORR_TF32 (1u << 1) /* edge-correction contractions on the tensor cores as 3xTF32 with
                                         FP32 accumulation (mma.sync m16n8k8); needs every corrected
                                         subdomain edge >= 2t. Default: FP32 CUDA-core products.   */
+#define MBS_FLAG_RESIDUAL_FORM (1u << 2) /* iterate on r'_n = Gamma^-1 (A x_n - y) instead of x_n:
+                                        r'_{n+1} = r'_n - alpha Gamma^-1 A r'_n, x_{n+1} = x_n - alpha r'_n
+                                        (compensated sum). The same iterates as Eq. wavesim_iter in exact
+                                        arithmetic; in complex64 the residual has no floor set by ||x||,
+                                        so tolerances below that floor are reachable. Costs about
+                                        24 B per voxel and iteration more (x and its low word).      */
 
 typedef struct mbs_options {
   int32_t truncation;        /* t, the kept edge width (Sec. 3, Fig. 5); 0 -> 8 (Sec. 3.3)      */

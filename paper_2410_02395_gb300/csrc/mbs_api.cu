@@ -129,6 +129,9 @@ struct mbs_plan {
   float *p2[3], *invn[3];
   int *sub[3], *loc[3], *sh2list, *lc[2];  // lc[d]: axis-d indices inside the layers, then outside
   float2* ebuf;  // e = x - w on the boundary layers
+  bool resform;  // residual form: the iteration runs on r' and accumulates x
+  float2* r;     // residual form: r'_n = Gamma^-1 (A x_n - y)
+  unsigned* xlo; // residual form: low word of x (two bfloat16)
   unsigned char* shell[3];
   int nsh2;
   float2* cW;
@@ -188,6 +191,9 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
   char* psrc = take(F);
   const bool corr = p->t > 0 && (p->a[0] > 0 || p->a[1] > 0 || p->a[2] > 0);
   char* pe = corr ? take(F) : nullptr;
+  const bool res = (p->flags & MBS_FLAG_RESIDUAL_FORM) != 0;
+  char* pr = res ? take(F) : nullptr;
+  char* pxl = res ? take((size_t)nvox(p) * sizeof(unsigned)) : nullptr;
   char *pp2[3], *pinv[3], *psub[3], *ploc[3], *psh[3];
   for (int d = 0; d < 3; d++) {
     pp2[d] = take(p->N[d] * sizeof(float));
@@ -226,6 +232,9 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
       p->shell[d] = (unsigned char*)psh[d];
     }
     p->ebuf = (float2*)pe;
+    p->resform = res;
+    p->r = (float2*)pr;
+    p->xlo = (unsigned*)pxl;
     p->sh2list = (int*)psh2;
     p->lc[0] = (int*)plc0;
     p->lc[1] = (int*)plc1;
@@ -612,8 +621,49 @@ cudaError_t run_rows_last(mbs_plan* p, PassArgs a, int mode, bool partials, Reco
   return cudaSuccess;
 }
 
+// One iteration in the residual form: with M = Gamma^-1 A = (I - V)(I - (L + I)^-1 (I - V)),
+// x_{n+1} = x_n - alpha r'_n and r'_{n+1} = r'_n - alpha M r'_n (r'_n = Gamma^-1 (A x_n - y)),
+// the same sequence as Eq. wavesim_iter computed on r' so that the transforms
+// work on O(||r'||) values instead of O(||x||).
+cudaError_t enqueue_iteration_res(mbs_plan* p, Recorder* rec) {
+  cudaError_t e;
+  PassArgs a = base_args(p);
+  a.X = p->r;
+  a.Xout = p->r;
+  a.Xs = p->x;
+  a.Xlo = p->xlo;
+  a.state = p->state;
+  if (p->has_shell) {
+    e = run_corr_rec(p, p->r, p->K, p->state, rec, KK_CORR_X, false);
+    if (e) return e;
+  }
+  e = run_transform_chain(p, a, FIRST_ITER, MID_PROP, rec);
+  if (e) return e;
+  e = run_rows_last(p, a, LAST_RES, true, rec, !p->has_shell);
+  if (e) return e;
+  if (p->has_shell) {
+    e = run_corr_rec(p, p->ebuf, p->K, p->state, rec, KK_CORR_E, true);
+    if (e) return e;
+    ShellArgs s = shell_args(p);
+    s.X = p->r;
+    s.state = p->state;
+    s.mode = SHELL_UPDATE_RES;
+    s.partials = p->partials;  // zeros: |r'_n|^2 was summed by the last pass
+    s.slot0 = p->n_rows_partials;
+    s.n_total = p->n_rows_partials + kShellBlocks;
+    s.fin = p->state;
+    s.hist = p->history;
+    if (rec) rec->begin(KK_SHELL_UPDATE);
+    e = launch_shell(s, kShellBlocks, p->stream);
+    if (rec) rec->end();
+    if (e) return e;
+  }
+  return cudaSuccess;
+}
+
 // One iteration of Eq. wavesim_iter on the plan's state (x, source).
 cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
+  if (p->resform) return enqueue_iteration_res(p, rec);
   cudaError_t e;
   PassArgs a = base_args(p);
   a.X = p->x;
@@ -966,6 +1016,13 @@ mbs_status mbs_set_source(mbs_plan* p, const void* source) {
   if (p->graph_ready) {  // the captured graph holds the source box: capture again
     cudaGraphExecDestroy(p->graph);
     p->graph_ready = false;
+  }
+  if (p->resform) {  // r'_0 = Gamma^-1 (A 0 - y) = -Gamma^-1 y, x_0 = 0 (hi and lo words)
+    CU(cudaMemsetAsync(p->xlo, 0, nv * sizeof(unsigned), p->stream));
+    mbs_status st = mbs_apply_operator(p, MBS_OP_PRECOND, p->x, p->r);
+    if (st) return st;
+    CU(launch_negate_copy(p->r, p->r, nv, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
   }
   return MBS_OK;
 }

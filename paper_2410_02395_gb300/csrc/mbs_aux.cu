@@ -439,7 +439,7 @@ cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st) {
 template <int U>
 __device__ __forceinline__ float shell_batch(const ShellArgs& a, const long long (&v)[U]) {
   const int mode = a.mode;
-  const bool upd = mode == SHELL_UPDATE_ITER || mode == SHELL_UPDATE_PRECOND;
+  const bool upd = mode == SHELL_UPDATE_ITER || mode == SHELL_UPDATE_PRECOND || mode == SHELL_UPDATE_RES;
   float2 ev[U], cv[U], xv[U], bv[U];
 #pragma unroll
   for (int u = 0; u < U; u++) {
@@ -448,7 +448,7 @@ __device__ __forceinline__ float shell_batch(const ShellArgs& a, const long long
     if (upd) {
       ev[u] = a.E[v[u]];
       bv[u] = a.B[v[u]];
-      if (mode == SHELL_UPDATE_ITER) xv[u] = a.X[v[u]];
+      if (mode == SHELL_UPDATE_ITER || mode == SHELL_UPDATE_RES) xv[u] = a.X[v[u]];
     } else if (mode == SHELL_ADD_E) {
       xv[u] = a.out[v[u]];
     }
@@ -457,7 +457,11 @@ __device__ __forceinline__ float shell_batch(const ShellArgs& a, const long long
 #pragma unroll
   for (int u = 0; u < U; u++) {
     if (v[u] < 0) continue;
-    if (upd) {
+    if (mode == SHELL_UPDATE_RES) {
+      // residual form: r'_{n+1} = r'_n - alpha (B e - E e); its |r'_n|^2 was summed by the last pass
+      const float2 r = csub(cmul(bv[u], ev[u]), cv[u]);
+      a.X[v[u]] = make_float2(fmaf(-a.alpha, r.x, xv[u].x), fmaf(-a.alpha, r.y, xv[u].y));
+    } else if (upd) {
       const float2 r = csub(cmul(bv[u], ev[u]), cv[u]);
       racc = fmaf(r.x, r.x, fmaf(r.y, r.y, racc));
       if (mode == SHELL_UPDATE_ITER)

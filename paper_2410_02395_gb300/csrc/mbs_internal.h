@@ -59,15 +59,17 @@ struct DevState {
 };
 
 enum FirstMode { FIRST_PLAIN = 0, FIRST_ITER = 1 };
-enum LastMode { LAST_PLAIN = 0, LAST_ITER = 1, LAST_PRECOND = 2, LAST_AOUT = 3 };
+enum LastMode { LAST_PLAIN = 0, LAST_ITER = 1, LAST_PRECOND = 2, LAST_AOUT = 3, LAST_RES = 4 };
 enum MidMode { MID_PROP = 0, MID_LSYM = 1, MID_FWD = 2, MID_INV = 3 };
-enum ShellMode { SHELL_UPDATE_ITER = 1, SHELL_UPDATE_PRECOND = 2, SHELL_ADD_E = 3, SHELL_SET_E = 4 };
+enum ShellMode { SHELL_UPDATE_ITER = 1, SHELL_UPDATE_PRECOND = 2, SHELL_ADD_E = 3, SHELL_SET_E = 4, SHELL_UPDATE_RES = 5 };
 
 struct PassArgs {
   float2* K;            // FFT buffer (on entry of the first pass: E x on the boundary layers)
   float2* E;            // e = x - w on the boundary layers (written by the last pass)
   const float2* X;      // field input
   float2* Xout;         // updated field or operator output
+  float2* Xs;           // residual form: the solution x (high word); X, Xout hold r' there
+  unsigned* Xlo;        // residual form: low word of x, two bfloat16 (real, imaginary)
   const float2* B;      // medium factor 1 - c(k^2 - k0^2)
   const float2* S;      // source map (may be null)
   int64_t sbox[6];      // [lo0, hi0, lo1, hi1, lo2, hi2) support of S

@@ -19,6 +19,8 @@
 #include <mutex>
 #include <unordered_map>
 
+#include <cuda_bf16.h>
+
 #include "mbs_fft.cuh"
 #include "mbs_internal.h"
 #include "mbs_reduce.cuh"
@@ -50,6 +52,24 @@ __device__ __forceinline__ float2 (*tile_of(float2* dyn))[kPad] {
 // issued in chunks of CH independent loads per thread (memory-level
 // parallelism), then consumed.
 // ---------------------------------------------------------------------------
+// x <- x + d with x = hi + lo (lo two bfloat16): TwoSum of hi and (d + lo), the
+// rounding error kept in lo, so that thousands of small updates do not lose
+// the bits FP32 alone would drop.
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+  const float s = a + b, bb = s - a;
+  err = (a - (s - bb)) + (b - bb);
+  return s;
+}
+__device__ __forceinline__ float2 acc_update(float2 hi, unsigned& lo, float2 d) {
+  const __nv_bfloat162 l = *reinterpret_cast<const __nv_bfloat162*>(&lo);
+  const float2 lf = __bfloat1622float2(l);
+  float ex, ey;
+  const float2 s = make_float2(two_sum(hi.x, d.x + lf.x, ex), two_sum(hi.y, d.y + lf.y, ey));
+  const __nv_bfloat162 nl = __floats2bfloat162_rn(ex, ey);
+  lo = *reinterpret_cast<const unsigned*>(&nl);
+  return s;
+}
+
 struct RowInfo {
   long long base;  // global index of element 0 of the segment
   int flags;       // bit0 valid, bit1 row inside an axis-0/1 boundary layer, bit2 row inside the source box
@@ -260,19 +280,27 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
   const float2* __restrict__ B = a.B;
   const bool need_x = mode != LAST_PLAIN;
   const bool need_b = mode != LAST_PLAIN;
+  const bool res = mode == LAST_RES;
   for (int k0 = 0; k0 < PERT; k0 += CH) {
-    float2 xv[CH], bv[CH];
+    float2 xv[CH], bv[CH], sv[CH];
+    unsigned lv[CH];
 #pragma unroll
     for (int c = 0; c < CH; c++) {
       const int idx = tid + (k0 + c) * NT;
       xv[c] = make_float2(0.f, 0.f);
       bv[c] = make_float2(0.f, 0.f);
+      sv[c] = make_float2(0.f, 0.f);
+      lv[c] = 0u;
       if (idx < 32 * N) {
         const int r = idx / N, e = idx - r * N;
         if (ri[r].flags & 1) {
           const long long gi = ri[r].base + e;
           if (need_x) xv[c] = X[gi];
           if (need_b) bv[c] = __ldg(B + gi);
+          if (res) {
+            sv[c] = a.Xs[gi];
+            lv[c] = a.Xlo[gi];
+          }
         }
       }
     }
@@ -289,6 +317,19 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
         a.Xout[gi] = w;
       } else if (mode == LAST_AOUT) {
         a.Xout[gi] = cadd(w, cmul(make_float2(1.f - bv[c].x, -bv[c].y), xv[c]));
+      } else if (res) {
+        // residual form: xv = r'_n, e = r' - w, r'_{n+1} = r' - alpha (I - V) e,
+        // x_{n+1} = x_n - alpha r'_n; |r'_n|^2 of every voxel is summed here
+        acc = fmaf(xv[c].x, xv[c].x, fmaf(xv[c].y, xv[c].y, acc));
+        a.Xs[gi] = acc_update(sv[c], lv[c], make_float2(-a.alpha * xv[c].x, -a.alpha * xv[c].y));
+        a.Xlo[gi] = lv[c];
+        const float2 ee = csub(xv[c], w);
+        if ((f & 2) || in_layer2<N>(a, e)) {
+          a.E[gi] = ee;  // r' on the layers is finished by the layer update
+        } else {
+          const float2 rr = cmul(bv[c], ee);
+          a.Xout[gi] = make_float2(fmaf(-a.alpha, rr.x, xv[c].x), fmaf(-a.alpha, rr.y, xv[c].y));
+        }
       } else {
         const float2 ee = csub(xv[c], w);
         if ((f & 2) || in_layer2<N>(a, e)) {

@@ -54,17 +54,23 @@ CASES = {
 
 
 TF32_CASES = ["cube_2x2x2", "uneven_sizes", "single_nonperiodic", "periodic_split_seam"]
+RES_CASES = ["cube_2x2x2", "single_periodic", "ragged_3x1x2", "line_1d"]
 
 
-@pytest.fixture(scope="module", params=sorted(CASES) + ["tf32:" + c for c in TF32_CASES])
+@pytest.fixture(scope="module", params=sorted(CASES) + ["tf32:" + c for c in TF32_CASES] +
+                ["res:" + c for c in RES_CASES])
 def pair(request):
     """(plan, oracle) on one case; "tf32:" cases run the edge corrections as 3xTF32
-    tensor-core products (same tolerances: the split recovers FP32 accuracy)."""
+    tensor-core products (same tolerances: the split recovers FP32 accuracy);
+    "res:" cases iterate in the residual form (same iterates in exact arithmetic)."""
     name = request.param
     kw = {}
     if name.startswith("tf32:"):
         name = name[5:]
         kw["corr_tf32"] = True
+    if name.startswith("res:"):
+        name = name[4:]
+        kw["residual_form"] = True
     plan, ref, n = make_pair(**CASES[name], **kw)
     yield plan, ref
     plan.close()
@@ -165,6 +171,26 @@ def test_solve_to_tolerance_small():
     h = np.array(hist)
     assert np.all(h[1:] <= h[:-1] * (1 + 1e-4) + 1e-6)   # monotone up to FP32 rounding
     plan.close()
+
+
+def test_residual_form_reaches_below_the_x_form_floor():
+    """The residual form converges to a tolerance the complex64 x-form cannot reach,
+    to the oracle's converged solution of the same truncated system."""
+    kw = dict(split=(2, 2, 1), widths=((3, 3), (3, 3), (2, 2)), t=4, seed=9)
+    plan, ref, n = make_pair((24, 20, 16), residual_form=True, **kw)
+    src = point_source(ref.shape)
+    x, it, res = plan.solve(torch.from_numpy(src).cuda(), tol=1e-8, max_iter=20000)
+    xr, itr, _ = ref.solve(src, tol=1e-11, max_iter=40000)
+    assert res < 1e-8
+    # the error of x is bounded by the conditioning of Gamma^-1 A times the gap
+    # between the recursive and the true residual (complex64 rounding of the
+    # transforms, summed over the iterations), ~1e-6 here
+    assert relative_l2(x.cpu().numpy(), xr) < 5e-6
+    plan.close()
+    plain, _, _ = make_pair((24, 20, 16), **kw)
+    _, it_x, res_x = plain.solve(torch.from_numpy(src).cuda(), tol=1e-8, max_iter=it)
+    assert res_x > 1e-8   # the x-form stalls above it within the same iteration budget
+    plain.close()
 
 
 def test_host_buffers_equal_device_buffers():
