@@ -36,6 +36,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = "C2"
+WORKLOAD_TEXT = {
+    "C1": "C1: 64^3 grid at lambda/4, one periodic subdomain, 6 spheres, 8-px absorbing layers, point source",
+    "C2": "C2: 256^3 grid at lambda/4, 2x2x2 subdomains of 128^3, t=8, 40 spheres, 8-px absorbing layers, point source",
+    "C3": "C3: 512^3 grid at lambda/4, 4x4x4 subdomains of 128^3, t=8, n = 1.33 + Gaussian random field, "
+          "Gaussian-beam plane source",
+    "C5": "C5: 1280^3 grid at lambda/4, 4x4x4 subdomains of 320^3, t=8, spheres to 30% fill, point source",
+}
 METRIC = "voxel-iterations/s on 1 GB300 (mixed vs plain FP32, ≤1e-4 vs FP64); time-to-tol"
 UNIT = "voxel-iterations/s"
 
@@ -133,10 +140,10 @@ def dist_env():
     return ws, rank, local
 
 
-def build_problem():
+def build_problem(name):
     from synth import config_problem
 
-    return config_problem(WORKLOAD)
+    return config_problem(name)
 
 
 def cpu_oracle_sample(iters=3, shape=(128, 128, 128)):
@@ -203,7 +210,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--e2e-iters", type=int, default=100, help="iterations per mbs_solve call in the e2e leg")
@@ -212,6 +219,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance leg")
     ap.add_argument("--ttt-max-iter", type=int, default=40000)
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_TEXT),
+                    help="benchmark workload (default: the C2 configuration)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 3xTF32-correction timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -231,7 +241,7 @@ def main():
     torch.cuda.set_device(dev)
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
-    params, n, src = build_problem()
+    params, n, src = build_problem(args.workload)
     shape = params["shape"]
     vox = int(np.prod(shape))
     stream = torch.cuda.Stream(device=dev)
@@ -306,16 +316,45 @@ def main():
                    "step": "one mbs_solve call: pinned host source -> device, %d iterations, field -> pinned host"
                            % args.e2e_iters}
 
-        # ---- time to tolerance ------------------------------------------------
+        plan.close()
+        n_dev = torch.from_numpy(n).to(dev)
+        kw = dict(boundary_widths=params["widths"], split=params["split"], truncation=params["t"],
+                  periodic=params["periodic"], stream=stream.cuda_stream)
+
+        # ---- the mixed form: 3xTF32 tensor-core edge corrections ---------------
+        mixed = None
+        if not args.no_mixed and info["a"] != [0, 0, 0]:
+            pm = pkg.Plan(shape, params["pixel"], params["wavelength"], n_dev, corr_tf32=True, **kw)
+            pm.set_source(src_dev)
+            pm.iterate(max(args.warmup, 3), 0.0, no_poll=True)
+            if ws > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize(dev)
+            ev0.record(stream)
+            pm.iterate(K, 0.0, no_poll=True)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            msm = ev0.elapsed_time(ev1)
+            if ws > 1:
+                tm = torch.tensor([msm], device=dev)
+                torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
+                msm = float(tm.item())
+            pm.close()
+            mixed = {"value": vox * K * ws / (msm / 1e3), "unit": UNIT, "ms_per_step": msm / K,
+                     "corrections": "3xTF32 mma.sync m16n8k8, FP32 accumulate"}
+
+        # ---- time to tolerance (residual form: no complex64 floor) -----------
         ttt_line = None
         if not args.no_ttt:
-            plan.set_source(src_dev)
+            pr = pkg.Plan(shape, params["pixel"], params["wavelength"], n_dev, residual_form=True, **kw)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            st_tol, it_tol, eps_tol = plan.iterate(args.ttt_max_iter, params["tol"])
+            pr.set_source(src_dev)
+            st_tol, it_tol, eps_tol = pr.iterate(args.ttt_max_iter, params["tol"])
             torch.cuda.synchronize(dev)
             ttt_line = {"tol": params["tol"], "status": st_tol, "iterations": it_tol, "residual": eps_tol,
-                        "seconds": time.perf_counter() - t0}
+                        "seconds": time.perf_counter() - t0, "form": "residual form, FP32 corrections"}
+            pr.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -328,10 +367,12 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64", "data": "synthetic",
-            "config": {"workload": "C2: 256^3 grid at lambda/4, 2x2x2 subdomains of 128^3, t=8, 40 spheres, "
-                                   "8-px absorbing layers, point source",
+            "config": {"workload": WORKLOAD_TEXT[args.workload],
                        "grid": list(shape), "split": list(params["split"]), "t": params["t"],
-                       "l2": "no flush: x, B and the FFT buffer are 134 MB each (> 129 MB L2)",
+                       "l2": ("no flush: x, B and the FFT buffer are %.0f MB each (> 129 MB L2)" % (vox * 8 / 1e6))
+                       if vox * 8 > 129e6 else
+                       ("working set of %.0f MB fits in L2 (not flushed): not a DRAM-bound measurement"
+                        % (5 * vox * 8 / 1e6)),
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "graph_iters": G},
             "clocks": clk,
@@ -339,12 +380,12 @@ def main():
             "roofline": roofline,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "mixed": mixed,
             "time_to_tol": ttt_line,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
-    plan.close()
     return 0
 
 

@@ -228,12 +228,12 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
 // e = x - w; away from the boundary layers r = B e, x <- x - alpha r and the
 // FP64 |r|^2; on the layers e is stored for the correction step.
 // ---------------------------------------------------------------------------
-template <int N>
+template <int N, bool RES>
 __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_last(const __grid_constant__ PassArgs a) {
   constexpr int W = warps_for(N);
   constexpr int NT = 32 * W;
   constexpr int PERT = (32 * N + NT - 1) / NT;
-  constexpr int CH = PERT < 8 ? PERT : 8;
+  constexpr int CH = RES ? (PERT < 4 ? PERT : 4) : (PERT < 8 ? PERT : 8);  // fewer staged voxels when x is staged too
   extern __shared__ float2 dyn[];
   float2 (*sm)[kPad] = tile_of<N>(dyn);
   __shared__ RowInfo ri[32];
@@ -280,24 +280,26 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
   const float2* __restrict__ B = a.B;
   const bool need_x = mode != LAST_PLAIN;
   const bool need_b = mode != LAST_PLAIN;
-  const bool res = mode == LAST_RES;
+  constexpr int CR = RES ? CH : 1;  // the residual form also stages x (high and low words)
   for (int k0 = 0; k0 < PERT; k0 += CH) {
-    float2 xv[CH], bv[CH], sv[CH];
-    unsigned lv[CH];
+    float2 xv[CH], bv[CH], sv[CR];
+    unsigned lv[CR];
 #pragma unroll
     for (int c = 0; c < CH; c++) {
       const int idx = tid + (k0 + c) * NT;
       xv[c] = make_float2(0.f, 0.f);
       bv[c] = make_float2(0.f, 0.f);
-      sv[c] = make_float2(0.f, 0.f);
-      lv[c] = 0u;
+      if constexpr (RES) {
+        sv[c] = make_float2(0.f, 0.f);
+        lv[c] = 0u;
+      }
       if (idx < 32 * N) {
         const int r = idx / N, e = idx - r * N;
         if (ri[r].flags & 1) {
           const long long gi = ri[r].base + e;
           if (need_x) xv[c] = X[gi];
           if (need_b) bv[c] = __ldg(B + gi);
-          if (res) {
+          if constexpr (RES) {
             sv[c] = a.Xs[gi];
             lv[c] = a.Xlo[gi];
           }
@@ -317,18 +319,20 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
         a.Xout[gi] = w;
       } else if (mode == LAST_AOUT) {
         a.Xout[gi] = cadd(w, cmul(make_float2(1.f - bv[c].x, -bv[c].y), xv[c]));
-      } else if (res) {
-        // residual form: xv = r'_n, e = r' - w, r'_{n+1} = r' - alpha (I - V) e,
-        // x_{n+1} = x_n - alpha r'_n; |r'_n|^2 of every voxel is summed here
-        acc = fmaf(xv[c].x, xv[c].x, fmaf(xv[c].y, xv[c].y, acc));
-        a.Xs[gi] = acc_update(sv[c], lv[c], make_float2(-a.alpha * xv[c].x, -a.alpha * xv[c].y));
-        a.Xlo[gi] = lv[c];
-        const float2 ee = csub(xv[c], w);
-        if ((f & 2) || in_layer2<N>(a, e)) {
-          a.E[gi] = ee;  // r' on the layers is finished by the layer update
-        } else {
-          const float2 rr = cmul(bv[c], ee);
-          a.Xout[gi] = make_float2(fmaf(-a.alpha, rr.x, xv[c].x), fmaf(-a.alpha, rr.y, xv[c].y));
+      } else if (RES) {
+        if constexpr (RES) {
+          // residual form: xv = r'_n, e = r' - w, r'_{n+1} = r' - alpha (I - V) e,
+          // x_{n+1} = x_n - alpha r'_n; |r'_n|^2 of every voxel is summed here
+          acc = fmaf(xv[c].x, xv[c].x, fmaf(xv[c].y, xv[c].y, acc));
+          a.Xs[gi] = acc_update(sv[c], lv[c], make_float2(-a.alpha * xv[c].x, -a.alpha * xv[c].y));
+          a.Xlo[gi] = lv[c];
+          const float2 ee = csub(xv[c], w);
+          if ((f & 2) || in_layer2<N>(a, e)) {
+            a.E[gi] = ee;  // r' on the layers is finished by the layer update
+          } else {
+            const float2 rr = cmul(bv[c], ee);
+            a.Xout[gi] = make_float2(fmaf(-a.alpha, rr.x, xv[c].x), fmaf(-a.alpha, rr.y, xv[c].y));
+          }
         }
       } else {
         const float2 ee = csub(xv[c], w);
@@ -475,9 +479,9 @@ inline size_t tile_bytes(int n) { return (size_t)n * kPad * sizeof(float2); }
 // (forward + multiplier + inverse keeps more values live than a single pass).
 constexpr int mid_min_blocks(int n) { return 24 / warps_for(n) > 1 ? 24 / warps_for(n) : 1; }
 
-// Per kernel (keyed by its address): the largest shared-memory carveout
-// (several tiles per SM) and, above 48 KB, the dynamic shared-memory opt-in
-// for the largest size requested so far.
+// Per kernel (keyed by its address): above 48 KB, the dynamic shared-memory
+// opt-in for the largest size requested so far. The L1/shared split is left to
+// the driver: these kernels read twiddles, tables and B through L1.
 struct KernelAttrs {
   std::mutex mu;
   std::unordered_map<const void*, size_t> smem;     // opted-in dynamic bytes
@@ -495,10 +499,7 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
   auto it = ka.smem.find(key);
   if (it != ka.smem.end() && it->second >= bytes) return cudaSuccess;
   cudaError_t e = cudaSuccess;
-  if (it == ka.smem.end())
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-  if (e == cudaSuccess && bytes > 48 * 1024)
+  if (bytes > 48 * 1024)
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) ka.smem[key] = bytes;
   return e;
@@ -520,9 +521,15 @@ cudaError_t run_size(int kind, int axis, bool inv, const PassArgs& a, int nrow_b
       break;
     }
     case 1: {
-      e = set_smem(k_rows_last<N>, sm);
-      if (e) return e;
-      k_rows_last<N><<<dim3(nrow_blocks, a.nsub), blk, sm, st>>>(a);
+      if (a.mode == LAST_RES) {
+        e = set_smem(k_rows_last<N, true>, sm);
+        if (e) return e;
+        k_rows_last<N, true><<<dim3(nrow_blocks, a.nsub), blk, sm, st>>>(a);
+      } else {
+        e = set_smem(k_rows_last<N, false>, sm);
+        if (e) return e;
+        k_rows_last<N, false><<<dim3(nrow_blocks, a.nsub), blk, sm, st>>>(a);
+      }
       break;
     }
     case 2: {
