@@ -229,6 +229,29 @@ MBS_API const char *mbs_kernel_kind_name(int32_t kind);
 MBS_API mbs_status mbs_apply_edge_corrections_noalloc(const mbs_plan *plan, const void *x, void *out);
 MBS_API const char *mbs_noalloc_last_error(void);
 
+/*
+ * Batches of independent solves (e.g. the frequencies of a transient
+ * simulation, which the paper solves one by one, Sec. 1), advanced together:
+ * one CUDA graph holds graph_iters iterations of every plan, each plan on its
+ * own stream forked from the batch stream so the solves run concurrently. Every
+ * plan keeps its own source (mbs_set_source), state, stop test and history; a
+ * converged plan's kernels leave at once. Plans must live on the current device
+ * and must not be iterated elsewhere while the batch runs. stream: NULL -> a
+ * stream the batch creates. graph_iters: 0 -> 10.
+ */
+typedef struct mbs_batch mbs_batch;
+MBS_API mbs_status mbs_batch_create(mbs_batch **batch, int32_t nplans, mbs_plan *const *plans, void *stream,
+                                    int32_t graph_iters);
+/*
+ * Run up to n_iter iterations of every plan (as mbs_iterate); per plan
+ * (nullable arrays of nplans entries): total iterations, last residual, status
+ * (MBS_OK reached tol, MBS_ENOCONV, MBS_ENAN, MBS_EDIVERGE). Returns MBS_OK if
+ * every plan reached tol, MBS_ENOCONV if some did not, or the first error.
+ */
+MBS_API mbs_status mbs_batch_iterate(mbs_batch *batch, int32_t n_iter, double tol, int32_t no_poll, int32_t *iters,
+                                     double *residuals, int32_t *statuses);
+MBS_API void mbs_batch_destroy(mbs_batch *batch);
+
 MBS_API void mbs_plan_destroy(mbs_plan *plan);
 
 /* Thread-local description of the last error (empty string if none). */

@@ -15,7 +15,7 @@ import os
 
 import numpy as np
 
-__all__ = ["Plan", "MBSError", "load_library", "OP", "STATUS", "build"]
+__all__ = ["Plan", "Batch", "MBSError", "load_library", "OP", "STATUS", "build"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_lib", "libmbs_gb300.so")
@@ -82,13 +82,17 @@ def load_library(path=None):
     lib.mbs_profile_iterations.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(dbl)]
     lib.mbs_kernel_kind_name.argtypes = [i32]
     lib.mbs_kernel_kind_name.restype = C.c_char_p
+    lib.mbs_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), vp, i32]
+    lib.mbs_batch_iterate.argtypes = [vp, i32, dbl, i32, C.POINTER(i32), C.POINTER(dbl), C.POINTER(i32)]
+    lib.mbs_batch_destroy.argtypes = [vp]
+    lib.mbs_batch_destroy.restype = None
     lib.mbs_plan_destroy.argtypes = [vp]
     lib.mbs_plan_destroy.restype = None
     lib.mbs_last_error.argtypes = []
     lib.mbs_last_error.restype = C.c_char_p
     for name in ("mbs_plan_create", "mbs_workspace_bytes", "mbs_plan_get_info", "mbs_apply_operator",
                  "mbs_set_source", "mbs_iterate", "mbs_get_field", "mbs_get_history", "mbs_solve",
-                 "mbs_profile_iterations"):
+                 "mbs_profile_iterations", "mbs_batch_create", "mbs_batch_iterate"):
         getattr(lib, name).restype = C.c_int
     if path is None:
         _lib = lib
@@ -293,3 +297,39 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Several plans advanced together (``mbs_batch_*`` in include/mbs.h)."""
+
+    def __init__(self, plans, stream=None, graph_iters=0):
+        self.lib = load_library()
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
+        h = C.c_void_p()
+        _check(self.lib, self.lib.mbs_batch_create(C.byref(h), len(self.plans), arr,
+                                                   C.c_void_p(int(stream)) if stream is not None else None,
+                                                   int(graph_iters)))
+        self.handle = h
+
+    def iterate(self, n_iter, tol=0.0, no_poll=False):
+        """Returns a list of (status_name, iterations, residual), one per plan."""
+        n = len(self.plans)
+        it = (C.c_int32 * n)()
+        res = (C.c_double * n)()
+        sts = (C.c_int32 * n)()
+        _check(self.lib, self.lib.mbs_batch_iterate(self.handle, int(n_iter), float(tol), 1 if no_poll else 0,
+                                                    it, res, sts), ok=(0, 4))
+        return [(STATUS[sts[i]], it[i], res[i]) for i in range(n)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.mbs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -149,6 +149,7 @@ struct mbs_plan {
   std::vector<SizeGroup> groups[3];
   int64_t sbox[6];
   bool have_source;
+  unsigned source_gen;  // incremented by every mbs_set_source (batches capture again)
   // graph
   cudaGraphExec_t graph;
   bool graph_ready;
@@ -1013,6 +1014,7 @@ mbs_status mbs_set_source(mbs_plan* p, const void* source) {
     for (int i = 0; i < 6; i++) p->sbox[i] = 0;
   }
   p->have_source = true;
+  p->source_gen += 1;
   if (p->graph_ready) {  // the captured graph holds the source box: capture again
     cudaGraphExecDestroy(p->graph);
     p->graph_ready = false;
@@ -1148,6 +1150,169 @@ mbs_status mbs_profile_iterations(mbs_plan* p, int32_t n_iter, int32_t launches[
     cudaEventDestroy(it.second.second);
   }
   return MBS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: several plans (independent solves, e.g. the frequencies of a
+// transient simulation, Sec. 1) advanced together. One CUDA graph holds G
+// iterations of every plan, each plan on its own stream forked from the batch
+// stream, so the solves' kernels run concurrently; a plan that has converged
+// leaves its kernels at once (its own stop flag).
+// ---------------------------------------------------------------------------
+struct mbs_batch {
+  std::vector<mbs_plan*> plans;
+  std::vector<unsigned> gen;
+  cudaStream_t stream;
+  bool own_stream;
+  cudaEvent_t fork;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t graph[2];  // G iterations, 1 iteration
+  bool ready[2];
+  int G;
+  DevState* host_states;
+};
+
+namespace {
+
+mbs_status batch_capture(mbs_batch* b, int which, int iters) {
+  if (b->ready[which]) {
+    cudaGraphExecDestroy(b->graph[which]);
+    b->ready[which] = false;
+  }
+  cudaGraph_t g;
+  CU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaEventRecord(b->fork, b->stream);
+  for (size_t i = 0; i < b->plans.size() && !e; i++) {
+    mbs_plan* p = b->plans[i];
+    e = cudaStreamWaitEvent(p->stream, b->fork, 0);
+    for (int k = 0; k < iters && !e; k++) e = enqueue_iteration(p, nullptr);
+    if (!e) e = cudaEventRecord(b->join[i], p->stream);
+    if (!e) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+  }
+  const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  if (e) return fail(MBS_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+  if (e2) return fail(MBS_ECUDA, std::string("batch end capture: ") + cudaGetErrorString(e2));
+  e = cudaGraphInstantiate(&b->graph[which], g, 0);
+  cudaGraphDestroy(g);
+  if (e) return fail(MBS_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+  b->ready[which] = true;
+  return MBS_OK;
+}
+
+mbs_status batch_read_states(mbs_batch* b) {
+  for (size_t i = 0; i < b->plans.size(); i++)
+    CU(cudaMemcpyAsync(b->host_states + i, b->plans[i]->state, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream));
+  CU(cudaStreamSynchronize(b->stream));
+  return MBS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mbs_status mbs_batch_create(mbs_batch** out, int32_t nplans, mbs_plan* const* plans, void* stream,
+                            int32_t graph_iters) {
+  g_err.clear();
+  if (!out || nplans < 1 || !plans) return fail(MBS_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  for (int i = 0; i < nplans; i++)
+    if (!plans[i]) return fail(MBS_EINVAL, "null plan in batch");
+  mbs_batch* b = new mbs_batch();
+  b->plans.assign(plans, plans + nplans);
+  b->gen.assign(nplans, ~0u);
+  b->G = graph_iters > 0 ? graph_iters : 10;
+  b->ready[0] = b->ready[1] = false;
+  b->own_stream = stream == nullptr;
+  b->host_states = nullptr;
+  b->fork = nullptr;
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return fail(MBS_ECUDA, "stream creation failed");
+  }
+  b->join.assign(nplans, nullptr);
+  bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaMallocHost((void**)&b->host_states, nplans * sizeof(DevState)) == cudaSuccess;
+  for (int i = 0; i < nplans && ok; i++) ok = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    mbs_batch_destroy(b);
+    return fail(MBS_ECUDA, "batch event or pinned allocation failed");
+  }
+  *out = b;
+  return MBS_OK;
+}
+
+mbs_status mbs_batch_iterate(mbs_batch* b, int32_t n_iter, double tol, int32_t no_poll, int32_t* iters,
+                             double* residuals, int32_t* statuses) {
+  g_err.clear();
+  if (!b || n_iter < 0) return fail(MBS_EINVAL, "bad argument");
+  // graphs hold every plan's source box: capture again after any mbs_set_source
+  bool stale = false;
+  for (size_t i = 0; i < b->plans.size(); i++)
+    if (b->gen[i] != b->plans[i]->source_gen) stale = true;
+  if (stale) {
+    for (int w = 0; w < 2; w++)
+      if (b->ready[w]) {
+        cudaGraphExecDestroy(b->graph[w]);
+        b->ready[w] = false;
+      }
+    for (size_t i = 0; i < b->plans.size(); i++) b->gen[i] = b->plans[i]->source_gen;
+  }
+  for (mbs_plan* p : b->plans) CU(launch_state_arm(p->state, n_iter, tol, 0, kHistCap, b->stream));
+  int remaining = n_iter;
+  bool all_done = false;
+  if (remaining >= b->G) {
+    if (!b->ready[0]) {
+      mbs_status st = batch_capture(b, 0, b->G);
+      if (st) return st;
+    }
+    while (remaining >= b->G && !all_done) {
+      CU(cudaGraphLaunch(b->graph[0], b->stream));
+      remaining -= b->G;
+      if (!no_poll) {
+        mbs_status st = batch_read_states(b);
+        if (st) return st;
+        all_done = true;
+        for (size_t i = 0; i < b->plans.size(); i++) all_done = all_done && b->host_states[i].done;
+      }
+    }
+  }
+  if (remaining > 0 && !all_done) {
+    if (!b->ready[1]) {
+      mbs_status st = batch_capture(b, 1, 1);
+      if (st) return st;
+    }
+    for (int k = 0; k < remaining; k++) CU(cudaGraphLaunch(b->graph[1], b->stream));
+  }
+  mbs_status st = batch_read_states(b);
+  if (st) return st;
+  mbs_status worst = MBS_OK;
+  for (size_t i = 0; i < b->plans.size(); i++) {
+    const DevState& hs = b->host_states[i];
+    mbs_status si = hs.status ? (mbs_status)hs.status : (hs.iter > 0 && hs.eps < tol ? MBS_OK : MBS_ENOCONV);
+    if (iters) iters[i] = hs.iter;
+    if (residuals) residuals[i] = hs.eps;
+    if (statuses) statuses[i] = si;
+    if (si != MBS_OK && (worst == MBS_OK || si != MBS_ENOCONV)) worst = si;
+  }
+  if (worst == MBS_ENOCONV) g_err = "some solves did not reach tol";
+  return worst;
+}
+
+void mbs_batch_destroy(mbs_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (int w = 0; w < 2; w++)
+    if (b->ready[w]) cudaGraphExecDestroy(b->graph[w]);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->host_states) cudaFreeHost(b->host_states);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
 }
 
 void mbs_plan_destroy(mbs_plan* p) {

@@ -436,9 +436,9 @@ cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st) {
 // Two index spaces, both walked in batches of U voxels per thread with every
 // load issued first: (1) whole grid rows inside an axis-0/1 layer (warp per
 // row), (2) the axis-2 layer positions of all other rows, flattened.
-template <int U>
+template <int U, int MODE>
 __device__ __forceinline__ float shell_batch(const ShellArgs& a, const long long (&v)[U]) {
-  const int mode = a.mode;
+  constexpr int mode = MODE;
   const bool upd = mode == SHELL_UPDATE_ITER || mode == SHELL_UPDATE_PRECOND || mode == SHELL_UPDATE_RES;
   float2 ev[U], cv[U], xv[U], bv[U];
 #pragma unroll
@@ -477,7 +477,8 @@ __device__ __forceinline__ float shell_batch(const ShellArgs& a, const long long
   return racc;
 }
 
-__global__ void __launch_bounds__(256) k_shell(const __grid_constant__ ShellArgs a) {
+template <int MODE>
+__global__ void __launch_bounds__(256, 4) k_shell(const __grid_constant__ ShellArgs a) {
   __shared__ double red[8];
   if (a.state && a.state->done) return;
   constexpr int U = 4;
@@ -505,7 +506,7 @@ __global__ void __launch_bounds__(256) k_shell(const __grid_constant__ ShellArgs
         const long long k = k0 + lane + 32 * u;
         v[u] = k < N2 ? rb + k : -1;
       }
-      acc += (double)shell_batch<U>(a, v);
+      acc += (double)shell_batch<U, MODE>(a, v);
     }
   }
   // (2) axis-2 layer positions of rows outside the axis-0/1 layers, flattened
@@ -524,7 +525,7 @@ __global__ void __launch_bounds__(256) k_shell(const __grid_constant__ ShellArgs
         v[u] = (i0 * a.g.N1 + i1) * N2 + a.tb.sh2list[k];
       }
     }
-    acc += (double)shell_batch<U>(a, v);
+    acc += (double)shell_batch<U, MODE>(a, v);
   }
   if (a.partials) {
     const double s = block_sum(acc, red);
@@ -533,7 +534,13 @@ __global__ void __launch_bounds__(256) k_shell(const __grid_constant__ ShellArgs
 }
 
 cudaError_t launch_shell(const ShellArgs& a, int blocks, cudaStream_t st) {
-  k_shell<<<blocks, 256, 0, st>>>(a);
+  switch (a.mode) {
+    case SHELL_UPDATE_ITER: k_shell<SHELL_UPDATE_ITER><<<blocks, 256, 0, st>>>(a); break;
+    case SHELL_UPDATE_PRECOND: k_shell<SHELL_UPDATE_PRECOND><<<blocks, 256, 0, st>>>(a); break;
+    case SHELL_UPDATE_RES: k_shell<SHELL_UPDATE_RES><<<blocks, 256, 0, st>>>(a); break;
+    case SHELL_ADD_E: k_shell<SHELL_ADD_E><<<blocks, 256, 0, st>>>(a); break;
+    default: k_shell<SHELL_SET_E><<<blocks, 256, 0, st>>>(a); break;
+  }
   return cudaGetLastError();
 }
 

@@ -4,6 +4,7 @@ This package holds no arithmetic of the method: it only draws media (refractive
 index maps without absorbing layers) and sources from seeded generators.
 """
 from .media import (  # noqa: F401
+    frequency_batch,
     spheres_medium,
     fill_spheres_medium,
     gaussian_random_field_medium,

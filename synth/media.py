@@ -13,6 +13,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
+    "frequency_batch",
     "spheres_medium",
     "fill_spheres_medium",
     "gaussian_random_field_medium",
@@ -190,3 +191,53 @@ def config_problem(name, shape=None):
                   split=tuple(cfg["split"]), periodic=tuple(cfg["periodic"]),
                   widths=((w, w), (w, w), (w, w)), t=cfg["t"], tol=cfg["tol"])
     return params, n, src
+
+
+def _smooth7(v):
+    for p in (2, 3, 5, 7):
+        while v % p == 0 and v > 1:
+            v //= p
+    return v == 1
+
+
+def _split2(total, lo=8):
+    """Two 7-smooth parts of ``total``, as equal as possible (None if there are none)."""
+    best = None
+    for a in range(total // 2, lo - 1, -1):
+        b = total - a
+        if _smooth7(a) and _smooth7(b):
+            if best is None or abs(b - a) < abs(best[1] - best[0]):
+                best = (b, a) if b >= a else (a, b)
+    return best
+
+
+def frequency_batch(count=64, seed=104, box=24.0, lam_range=(0.8, 1.2), ppw=4, spheres=30,
+                    r_range=(1.0, 5.0), n_range=(1.0, 1.5), widths=8, t=8, tol=1e-5):
+    """Independent frequency solves on one physical box (transient simulations
+    solve every frequency separately, Sec. 1): wavelength uniform in
+    ``lam_range``, pixel lambda/ppw, grid round(box/pixel) (raised until it splits
+    into two 7-smooth halves per axis), split 2x2x2; the same seeded spheres
+    (centres, radii in the box's length unit) rasterised on every grid, a point
+    source at the centre. Returns a list of ``(params, n, source)``."""
+    rng = np.random.default_rng(seed)
+    lams = rng.uniform(*lam_range, size=count)
+    margin = 2.0
+    sph = [(rng.uniform(margin, box - margin, size=3), rng.uniform(*r_range), rng.uniform(*n_range))
+           for _ in range(spheres)]
+    out = []
+    for lam in lams:
+        h = lam / ppw
+        N = int(round(box / h))
+        while _split2(N) is None:
+            N += 1
+        sizes = list(_split2(N))
+        shp = (N, N, N)
+        n = np.ones(shp, dtype=np.complex64)
+        for c, r, v in sph:
+            _paint_sphere(n, [ci / h for ci in c], r / h, v)
+        src = point_source(shp)
+        params = dict(shape=shp, pixel=h, wavelength=float(lam), split=(2, 2, 2), periodic=(False,) * 3,
+                      widths=((widths, widths),) * 3, t=t, tol=tol, split_sizes=[sizes, sizes, sizes])
+        out.append((params, n, src))
+    return out
+
