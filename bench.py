@@ -41,6 +41,9 @@ WORKLOAD_TEXT = {
     "C2": "C2: 256^3 grid at lambda/4, 2x2x2 subdomains of 128^3, t=8, 40 spheres, 8-px absorbing layers, point source",
     "C3": "C3: 512^3 grid at lambda/4, 4x4x4 subdomains of 128^3, t=8, n = 1.33 + Gaussian random field, "
           "Gaussian-beam plane source",
+    "C4": "C4: 64 independent frequency solves, lambda uniform in [0.8,1.2] on one 24-unit box at lambda/4 "
+          "(grids 80^3-120^3), each split 2x2x2 into 7-smooth halves, t=8, same spheres, point sources; "
+          "one CUDA graph over all solves",
     "C5": "C5: 1280^3 grid at lambda/4, 4x4x4 subdomains of 320^3, t=8, spheres to 30% fill, point source",
 }
 METRIC = "voxel-iterations/s on 1 GB300 (mixed vs plain FP32, ≤1e-4 vs FP64); time-to-tol"
@@ -207,6 +210,85 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args, pkg, torch, ws, rank, dev):
+    """The C4 workload: 64 solves advanced together by one graph per G iterations,
+    against the same solves advanced one after another."""
+    import numpy as np
+
+    from synth import frequency_batch
+
+    problems = frequency_batch(count=64, seed=104)
+    stream = torch.cuda.Stream(device=dev)
+    plans = []
+    for params, n, src in problems:
+        p = pkg.Plan(params["shape"], params["pixel"], params["wavelength"], torch.from_numpy(n).to(dev),
+                     boundary_widths=params["widths"], split=params["split"], truncation=params["t"],
+                     periodic=params["periodic"], split_sizes=params["split_sizes"])
+        p.set_source(torch.from_numpy(src).to(dev))
+        plans.append(p)
+    vox = sum(int(np.prod(pp["shape"])) for pp, _, _ in problems)
+    G = 10
+    K = max(G, (args.steps // 10 // G) * G)
+    b = pkg.Batch(plans, stream=stream.cuda_stream, graph_iters=G)
+    b.iterate(max(args.warmup, 3), 0.0, no_poll=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ev0.record(stream)
+    b.iterate(K, 0.0, no_poll=True)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    value = vox * K * ws / (ms / 1e3)
+    # the same solves one after another, each with its own graph replays
+    t0 = time.perf_counter()
+    for p in plans:
+        p.iterate(K, 0.0, no_poll=True)
+    torch.cuda.synchronize(dev)
+    seq = time.perf_counter() - t0
+    # time to tolerance of all 64 solves (residual form), batched
+    ttt = None
+    if not args.no_ttt:
+        rplans = []
+        for params, n, src in problems:
+            p = pkg.Plan(params["shape"], params["pixel"], params["wavelength"], torch.from_numpy(n).to(dev),
+                         boundary_widths=params["widths"], split=params["split"], truncation=params["t"],
+                         periodic=params["periodic"], split_sizes=params["split_sizes"], residual_form=True)
+            rplans.append(p)
+        rb = pkg.Batch(rplans, graph_iters=G)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for p, (_, _, src) in zip(rplans, problems):
+            p.set_source(torch.from_numpy(src).to(dev))
+        res = rb.iterate(args.ttt_max_iter, problems[0][0]["tol"])
+        torch.cuda.synchronize(dev)
+        ttt = {"tol": problems[0][0]["tol"], "seconds": time.perf_counter() - t0,
+               "converged": sum(1 for r in res if r[0] == "MBS_OK"), "solves": len(res),
+               "iterations_max": max(r[1] for r in res), "iterations_min": min(r[1] for r in res),
+               "form": "residual form, FP32 corrections, one batch"}
+        rb.close()
+        for p in rplans:
+            p.close()
+    b.close()
+    for p in plans:
+        p.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+                "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "c64", "data": "synthetic",
+                "config": {"workload": WORKLOAD_TEXT["C4"], "solves": len(problems), "voxels": vox,
+                           "l2": "no flush: %.0f MB per field summed over the solves (> 129 MB L2)" % (vox * 8 / 1e6),
+                           "parallelism": "replicas" if ws > 1 else "single GPU", "graph_iters": G},
+                "clocks": clk,
+                "sequential": {"value": vox * K / seq, "unit": UNIT,
+                               "how": "the same 64 solves one after another, each with its own graph replays"},
+                "time_to_tol": ttt}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -241,6 +323,8 @@ def main():
     torch.cuda.set_device(dev)
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
+    if args.workload == "C4":
+        return run_batch(args, pkg, torch, ws, rank, dev)
     params, n, src = build_problem(args.workload)
     shape = params["shape"]
     vox = int(np.prod(shape))
