@@ -100,6 +100,27 @@ __device__ __forceinline__ void setup_rows(RowInfo* ri, const PassArgs& a, int o
   }
 }
 
+// Element (r, e) of a row tile (32 rows x N) handled by thread tid at step k.
+// When NT divides 32 N and N divides NT (NT = 2N for every N >= 64 that is a
+// multiple of 16), each thread keeps one element index e and walks rows
+// r, r + NT/N, ...; the rows stay below 32 for k < 32 N / NT.
+template <int N, int NT>
+struct TileMap {
+  static constexpr bool fixed = (NT % N) == 0 && ((32 * N) % NT) == 0;
+  __device__ __forceinline__ static bool at(int tid, int k, int& r, int& e) {
+    if constexpr (fixed) {
+      r = tid / N + k * (NT / N);
+      e = tid % N;
+      return r < 32;
+    } else {
+      const int idx = tid + k * NT;
+      r = idx / N;
+      e = idx - r * N;
+      return idx < 32 * N;
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Axis-2 forward pass with the fused medium/source/correction prologue:
 // u = B x + y - E x (FIRST_ITER) or u = x (FIRST_PLAIN), then the transform.
@@ -155,10 +176,10 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
     float2 xv[CH], bv[CH], cv[CH];
 #pragma unroll
     for (int c = 0; c < CH; c++) {
-      const int idx = tid + (k0 + c) * NT;
+      int r, e;
+      const bool ok = TileMap<N, NT>::at(tid, k0 + c, r, e);
       xv[c] = bv[c] = cv[c] = make_float2(0.f, 0.f);
-      if (idx < 32 * N) {
-        const int r = idx / N, e = idx - r * N;
+      if (ok) {
         const int f = ri[r].flags;
         if (f & 1) {
           const long long gi = ri[r].base + e;
@@ -172,9 +193,8 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
     }
 #pragma unroll
     for (int c = 0; c < CH; c++) {
-      const int idx = tid + (k0 + c) * NT;
-      if (idx < 32 * N) {
-        const int r = idx / N, e = idx - r * N;
+      int r, e;
+      if (TileMap<N, NT>::at(tid, k0 + c, r, e)) {
         const int f = ri[r].flags;
         float2 u = xv[c];
         if (iter && (f & 1)) {
@@ -215,11 +235,8 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
   }
   __syncthreads();
   for (int k0 = 0; k0 < PERT; k0++) {
-    const int idx = tid + k0 * NT;
-    if (idx < 32 * N) {
-      const int r = idx / N, e = idx - r * N;
-      if (ri[r].flags & 1) K[ri[r].base + e] = sm[e][r];
-    }
+    int r, e;
+    if (TileMap<N, NT>::at(tid, k0, r, e) && (ri[r].flags & 1)) K[ri[r].base + e] = sm[e][r];
   }
 }
 
@@ -249,20 +266,14 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
     float2 kv[CH];
 #pragma unroll
     for (int c = 0; c < CH; c++) {
-      const int idx = tid + (k0 + c) * NT;
+      int r, e;
       kv[c] = make_float2(0.f, 0.f);
-      if (idx < 32 * N) {
-        const int r = idx / N, e = idx - r * N;
-        if (ri[r].flags & 1) kv[c] = K[ri[r].base + e];
-      }
+      if (TileMap<N, NT>::at(tid, k0 + c, r, e) && (ri[r].flags & 1)) kv[c] = K[ri[r].base + e];
     }
 #pragma unroll
     for (int c = 0; c < CH; c++) {
-      const int idx = tid + (k0 + c) * NT;
-      if (idx < 32 * N) {
-        const int r = idx / N, e = idx - r * N;
-        sm[e][r] = kv[c];
-      }
+      int r, e;
+      if (TileMap<N, NT>::at(tid, k0 + c, r, e)) sm[e][r] = kv[c];
     }
   }
   if constexpr (N > 1) {
@@ -286,15 +297,15 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
     unsigned lv[CR];
 #pragma unroll
     for (int c = 0; c < CH; c++) {
-      const int idx = tid + (k0 + c) * NT;
+      int r, e;
+      const bool ok = TileMap<N, NT>::at(tid, k0 + c, r, e);
       xv[c] = make_float2(0.f, 0.f);
       bv[c] = make_float2(0.f, 0.f);
       if constexpr (RES) {
         sv[c] = make_float2(0.f, 0.f);
         lv[c] = 0u;
       }
-      if (idx < 32 * N) {
-        const int r = idx / N, e = idx - r * N;
+      if (ok) {
         if (ri[r].flags & 1) {
           const long long gi = ri[r].base + e;
           if (need_x) xv[c] = X[gi];
@@ -308,9 +319,8 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
     }
 #pragma unroll
     for (int c = 0; c < CH; c++) {
-      const int idx = tid + (k0 + c) * NT;
-      if (idx >= 32 * N) continue;
-      const int r = idx / N, e = idx - r * N;
+      int r, e;
+      if (!TileMap<N, NT>::at(tid, k0 + c, r, e)) continue;
       const int f = ri[r].flags;
       if (!(f & 1)) continue;
       const long long gi = ri[r].base + e;
