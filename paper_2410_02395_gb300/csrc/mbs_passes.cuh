@@ -70,34 +70,56 @@ __device__ __forceinline__ float2 acc_update(float2 hi, unsigned& lo, float2 d) 
   return s;
 }
 
-struct RowInfo {
-  long long base;  // global index of element 0 of the segment
-  int flags;       // bit0 valid, bit1 row inside an axis-0/1 boundary layer, bit2 row inside the source box
+// A row tile: 32 consecutive grid rows rho = i0*N1 + i1 from rho0, one axis-2
+// segment starting at off2. Row r starts at (rho0 + r) * N2 + off2; its flags
+// are bits of three 32-bit masks built by the first warp with ballots:
+// valid (inside the grid), layer (i0 or i1 inside an axis-0/1 boundary layer)
+// and src (inside the source box's rows).
+struct RowTile {
+  long long base0;  // rho0 * N2 + off2
+  long long N2;
+  unsigned valid, layer, src;
+  __device__ __forceinline__ long long base(int r) const { return base0 + (long long)r * N2; }
+  __device__ __forceinline__ bool ok(int r) const { return (valid >> r) & 1u; }
+  __device__ __forceinline__ bool lay(int r) const { return (layer >> r) & 1u; }
+  __device__ __forceinline__ bool in_src(int r) const { return (src >> r) & 1u; }
 };
+
+__device__ __forceinline__ RowTile setup_rows(unsigned* masks, const PassArgs& a, int off2) {
+  const int tid = threadIdx.x;
+  const long long rho0 = (long long)blockIdx.x * 32;
+  if (tid < 32) {
+    const long long rows = a.g.N0 * a.g.N1;
+    const long long rho = rho0 + tid;
+    bool v = false, l = false, sr = false;
+    if (rho < rows) {
+      const long long i0 = rho / a.g.N1, i1 = rho - i0 * a.g.N1;
+      v = true;
+      l = a.tb.shell[0][i0] | a.tb.shell[1][i1];
+      sr = a.S && i0 >= a.sbox[0] && i0 < a.sbox[1] && i1 >= a.sbox[2] && i1 < a.sbox[3];
+    }
+    const unsigned mv = __ballot_sync(0xffffffffu, v), ml = __ballot_sync(0xffffffffu, l),
+                   ms = __ballot_sync(0xffffffffu, sr);
+    if (tid == 0) {
+      masks[0] = mv;
+      masks[1] = ml;
+      masks[2] = ms;
+    }
+  }
+  __syncthreads();
+  RowTile t;
+  t.N2 = a.g.N2;
+  t.base0 = rho0 * a.g.N2 + off2;
+  t.valid = masks[0];
+  t.layer = masks[1];
+  t.src = masks[2];
+  return t;
+}
 
 // Element e of an axis-2 segment of length N lies in a boundary layer of that axis.
 template <int N>
 __device__ __forceinline__ bool in_layer2(const PassArgs& a, int e) {
   return a.g.ax[2].a > 0 && (e < a.g.t || e >= N - a.g.t);
-}
-
-__device__ __forceinline__ void setup_rows(RowInfo* ri, const PassArgs& a, int off2) {
-  const int tid = threadIdx.x;
-  if (tid < 32) {
-    const long long rows = a.g.N0 * a.g.N1;
-    const long long rho = (long long)blockIdx.x * 32 + tid;
-    RowInfo r;
-    r.flags = 0;
-    r.base = 0;
-    if (rho < rows) {
-      const long long i0 = rho / a.g.N1, i1 = rho - i0 * a.g.N1;
-      r.base = rho * a.g.N2 + off2;
-      r.flags = 1;
-      if (a.tb.shell[0][i0] | a.tb.shell[1][i1]) r.flags |= 2;
-      if (a.S && i0 >= a.sbox[0] && i0 < a.sbox[1] && i1 >= a.sbox[2] && i1 < a.sbox[3]) r.flags |= 4;
-    }
-    ri[tid] = r;
-  }
 }
 
 // Element (r, e) of a row tile (32 rows x N) handled by thread tid at step k.
@@ -125,7 +147,8 @@ struct TileMap {
 // Axis-2 forward pass with the fused medium/source/correction prologue:
 // u = B x + y - E x (FIRST_ITER) or u = x (FIRST_PLAIN), then the transform.
 // ---------------------------------------------------------------------------
-template <int N>
+// TC: compile-time truncation width of the fused axis-2 corrections (0: runtime t).
+template <int N, int TC>
 __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_first(const __grid_constant__ PassArgs a) {
   constexpr int W = warps_for(N);
   constexpr int NT = 32 * W;
@@ -133,13 +156,12 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
   constexpr int CH = PERT < 8 ? PERT : 8;
   extern __shared__ float2 dyn[];
   float2 (*sm)[kPad] = tile_of<N>(dyn);
-  __shared__ RowInfo ri[32];
+  __shared__ unsigned masks[3];
   if (a.state && a.state->done) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int j2 = a.subs[blockIdx.y];
   const int off2 = a.g.ax[2].off[j2];
-  setup_rows(ri, a, off2);
-  __syncthreads();
+  const RowTile rt = setup_rows(masks, a, off2);
   const bool iter = a.mode == FIRST_ITER;
   const float2* __restrict__ X = a.X;
   const float2* __restrict__ B = a.B;
@@ -148,7 +170,7 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
   // segment's own first/last t voxels and the neighbours' adjacent t voxels of
   // every row: fetched asynchronously into shared memory while the tile loads.
   const bool e2 = iter && a.fuse_e2 && a.g.ax[2].a > 0;
-  const int t = a.g.t;
+  const int t = TC > 0 ? TC : a.g.t;
   const AxisDesc& ax2 = a.g.ax[2];
   const int L = ax2.left[j2], R = ax2.right[j2];
   float2* xe = dyn + N * kPad;         // [32 rows][4t]: own first t, own last t, left's last t, right's first t
@@ -157,13 +179,13 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
     for (int idx = tid; idx < 32 * 4 * t; idx += NT) {
       const int r = idx / (4 * t), k = idx - r * 4 * t;
       long long pos = -1;
-      if (ri[r].flags & 1) {
+      if (rt.ok(r)) {
         if (k < t) pos = off2 + k;
         else if (k < 2 * t) pos = off2 + N - t + (k - t);
         else if (k < 3 * t) pos = L >= 0 ? ax2.off[L] + ax2.n[L] - t + (k - 2 * t) : -1;
         else pos = R >= 0 ? ax2.off[R] + (k - 3 * t) : -1;
       }
-      if (pos >= 0) cp_async8(xe + idx, X + (ri[r].base - off2) + pos);
+      if (pos >= 0) cp_async8(xe + idx, X + (rt.base(r) - off2) + pos);
       else xe[idx] = make_float2(0.f, 0.f);
     }
     cp_async_commit();
@@ -179,15 +201,12 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
       int r, e;
       const bool ok = TileMap<N, NT>::at(tid, k0 + c, r, e);
       xv[c] = bv[c] = cv[c] = make_float2(0.f, 0.f);
-      if (ok) {
-        const int f = ri[r].flags;
-        if (f & 1) {
-          const long long gi = ri[r].base + e;
-          xv[c] = __ldg(X + gi);
-          if (iter) {
-            bv[c] = __ldg(B + gi);
-            if ((f & 2) || (!a.fuse_e2 && in_layer2<N>(a, e))) cv[c] = K[gi];  // E x computed by the correction kernels
-          }
+      if (ok && rt.ok(r)) {
+        const long long gi = rt.base(r) + e;
+        xv[c] = __ldg(X + gi);
+        if (iter) {
+          bv[c] = __ldg(B + gi);
+          if (rt.lay(r) || (!a.fuse_e2 && in_layer2<N>(a, e))) cv[c] = K[gi];  // E x from the correction kernels
         }
       }
     }
@@ -195,12 +214,11 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
     for (int c = 0; c < CH; c++) {
       int r, e;
       if (TileMap<N, NT>::at(tid, k0 + c, r, e)) {
-        const int f = ri[r].flags;
         float2 u = xv[c];
-        if (iter && (f & 1)) {
+        if (iter && rt.ok(r)) {
           u = csub(cmul(bv[c], xv[c]), cv[c]);
           const long long i2 = off2 + e;
-          if ((f & 4) && i2 >= a.sbox[4] && i2 < a.sbox[5]) u = cadd(u, cmul(a.mc, a.S[ri[r].base + e]));
+          if (rt.in_src(r) && i2 >= a.sbox[4] && i2 < a.sbox[5]) u = cadd(u, cmul(a.mc, a.S[rt.base(r) + e]));
         }
         sm[e][r] = u;
       }
@@ -217,12 +235,24 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
       if (k >= t && q < t) continue;  // also in the first range (N < 2t): done there
       const float2* x4 = xe + r * 4 * t;
       float2 v = make_float2(0.f, 0.f);
-      if (q < t) {
-        for (int b = 0; b < t; b++) v = cadd(v, cmul(wsm[q - b + t - 1], csub(x4[2 * t + b], x4[t + b])));
-      }
-      if (q >= N - t) {
-        const int aa = q - (N - t);
-        for (int b = 0; b < t; b++) v = cadd(v, cmul(wsm[b - aa + t - 1], csub(x4[3 * t + b], x4[b])));
+      if constexpr (TC > 0) {
+        if (q < TC) {
+#pragma unroll
+          for (int b = 0; b < TC; b++) v = cadd(v, cmul(wsm[q - b + TC - 1], csub(x4[2 * TC + b], x4[TC + b])));
+        }
+        if (q >= N - TC) {
+          const int aa = q - (N - TC);
+#pragma unroll
+          for (int b = 0; b < TC; b++) v = cadd(v, cmul(wsm[b - aa + TC - 1], csub(x4[3 * TC + b], x4[b])));
+        }
+      } else {
+        if (q < t) {
+          for (int b = 0; b < t; b++) v = cadd(v, cmul(wsm[q - b + t - 1], csub(x4[2 * t + b], x4[t + b])));
+        }
+        if (q >= N - t) {
+          const int aa = q - (N - t);
+          for (int b = 0; b < t; b++) v = cadd(v, cmul(wsm[b - aa + t - 1], csub(x4[3 * t + b], x4[b])));
+        }
       }
       sm[q][r] = csub(sm[q][r], v);
     }
@@ -236,7 +266,7 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
   __syncthreads();
   for (int k0 = 0; k0 < PERT; k0++) {
     int r, e;
-    if (TileMap<N, NT>::at(tid, k0, r, e) && (ri[r].flags & 1)) K[ri[r].base + e] = sm[e][r];
+    if (TileMap<N, NT>::at(tid, k0, r, e) && rt.ok(r)) K[rt.base(r) + e] = sm[e][r];
   }
 }
 
@@ -253,14 +283,13 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
   constexpr int CH = RES ? (PERT < 4 ? PERT : 4) : (PERT < 8 ? PERT : 8);  // fewer staged voxels when x is staged too
   extern __shared__ float2 dyn[];
   float2 (*sm)[kPad] = tile_of<N>(dyn);
-  __shared__ RowInfo ri[32];
+  __shared__ unsigned masks[3];
   __shared__ double red[32];
   if (a.state && a.state->done) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int j2 = a.subs[blockIdx.y];
   const int off2 = a.g.ax[2].off[j2];
-  setup_rows(ri, a, off2);
-  __syncthreads();
+  const RowTile rt = setup_rows(masks, a, off2);
   float2* K = a.K;
   for (int k0 = 0; k0 < PERT; k0 += CH) {
     float2 kv[CH];
@@ -268,7 +297,7 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
     for (int c = 0; c < CH; c++) {
       int r, e;
       kv[c] = make_float2(0.f, 0.f);
-      if (TileMap<N, NT>::at(tid, k0 + c, r, e) && (ri[r].flags & 1)) kv[c] = K[ri[r].base + e];
+      if (TileMap<N, NT>::at(tid, k0 + c, r, e) && rt.ok(r)) kv[c] = K[rt.base(r) + e];
     }
 #pragma unroll
     for (int c = 0; c < CH; c++) {
@@ -306,8 +335,8 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
         lv[c] = 0u;
       }
       if (ok) {
-        if (ri[r].flags & 1) {
-          const long long gi = ri[r].base + e;
+        if (rt.ok(r)) {
+          const long long gi = rt.base(r) + e;
           if (need_x) xv[c] = X[gi];
           if (need_b) bv[c] = __ldg(B + gi);
           if constexpr (RES) {
@@ -320,10 +349,8 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
 #pragma unroll
     for (int c = 0; c < CH; c++) {
       int r, e;
-      if (!TileMap<N, NT>::at(tid, k0 + c, r, e)) continue;
-      const int f = ri[r].flags;
-      if (!(f & 1)) continue;
-      const long long gi = ri[r].base + e;
+      if (!TileMap<N, NT>::at(tid, k0 + c, r, e) || !rt.ok(r)) continue;
+      const long long gi = rt.base(r) + e;
       const float2 w = sm[e][r];
       if (mode == LAST_PLAIN) {
         a.Xout[gi] = w;
@@ -337,7 +364,7 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
           a.Xs[gi] = acc_update(sv[c], lv[c], make_float2(-a.alpha * xv[c].x, -a.alpha * xv[c].y));
           a.Xlo[gi] = lv[c];
           const float2 ee = csub(xv[c], w);
-          if ((f & 2) || in_layer2<N>(a, e)) {
+          if (rt.lay(r) || in_layer2<N>(a, e)) {
             a.E[gi] = ee;  // r' on the layers is finished by the layer update
           } else {
             const float2 rr = cmul(bv[c], ee);
@@ -346,7 +373,7 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_l
         }
       } else {
         const float2 ee = csub(xv[c], w);
-        if ((f & 2) || in_layer2<N>(a, e)) {
+        if (rt.lay(r) || in_layer2<N>(a, e)) {
           a.E[gi] = ee;  // finished by the layer update once all of e is known
         } else {
           const float2 rr = cmul(bv[c], ee);
@@ -525,9 +552,16 @@ cudaError_t run_size(int kind, int axis, bool inv, const PassArgs& a, int nrow_b
     case 0: {
       // tile, then the axis-2 edge values [32][4t] and the 2t-1 Toeplitz weights
       const size_t edge = a.g.ax[2].a > 0 ? ((size_t)32 * 4 * a.g.t + 2 * a.g.t) * sizeof(float2) : 0;
-      e = set_smem(k_rows_first<N>, sm + ((size_t)32 * 4 * kMaxT + 2 * kMaxT) * sizeof(float2));
-      if (e) return e;
-      k_rows_first<N><<<dim3(nrow_blocks, a.nsub), blk, sm + edge, st>>>(a);
+      const size_t smax = sm + ((size_t)32 * 4 * kMaxT + 2 * kMaxT) * sizeof(float2);
+      if (a.g.t == 8) {
+        e = set_smem(k_rows_first<N, 8>, smax);
+        if (e) return e;
+        k_rows_first<N, 8><<<dim3(nrow_blocks, a.nsub), blk, sm + edge, st>>>(a);
+      } else {
+        e = set_smem(k_rows_first<N, 0>, smax);
+        if (e) return e;
+        k_rows_first<N, 0><<<dim3(nrow_blocks, a.nsub), blk, sm + edge, st>>>(a);
+      }
       break;
     }
     case 1: {
