@@ -50,10 +50,15 @@ CASES = {
     "plane_2d": dict(shape=(1, 40, 64), split=(1, 2, 2), t=4, periodic=(True, False, False),
                      widths=((0, 0), (4, 4), (4, 4))),
     "tiny_t1": dict(shape=(12, 10, 8), split=(2, 2, 2), t=1),
+    # truncation sweep (Sec. 4.2.1): wider corrections on the same geometry
+    "t_sweep_2": dict(shape=(64, 48, 40), split=(2, 2, 2), t=2),
+    "t_sweep_6": dict(shape=(64, 48, 40), split=(2, 2, 2), t=6),
+    "t_sweep_12": dict(shape=(64, 48, 40), split=(2, 2, 2), t=12),
+    "t_sweep_16": dict(shape=(64, 48, 40), split=(2, 2, 2), t=16),
 }
 
 
-TF32_CASES = ["cube_2x2x2", "uneven_sizes", "single_nonperiodic", "periodic_split_seam"]
+TF32_CASES = ["cube_2x2x2", "uneven_sizes", "single_nonperiodic", "periodic_split_seam", "t_sweep_6"]
 RES_CASES = ["cube_2x2x2", "single_periodic", "ragged_3x1x2", "line_1d"]
 
 
@@ -227,3 +232,57 @@ def test_invalid_inputs_are_errors():
     with pytest.raises(pkg.MBSError) as ei:
         pkg.Plan((8, 8, 8), 0.25, 1.0, torch.from_numpy(n).cuda(), split=(2, 1, 1), truncation=5)
     assert ei.value.status == 1
+
+
+def test_nan_in_the_source_is_reported():
+    """A non-finite residual stops the iteration with MBS_ENAN (fault made on the host)."""
+    pkg = _pkg()
+    plan, ref, n = make_pair((16, 16, 16), split=(2, 1, 1), t=2, seed=4)
+    src = point_source(ref.shape)
+    src[3, 3, 3] = np.nan
+    with pytest.raises(pkg.MBSError) as ei:
+        plan.solve(torch.from_numpy(src).cuda(), tol=1e-6, max_iter=50)
+    assert ei.value.status == 5
+    plan.close()
+
+
+def test_over_relaxation_is_reported_as_divergence():
+    """alpha = 4 breaks the convergence condition (alpha <= 1, Sec. 2): the residual
+    keeps rising and the solve stops with MBS_EDIVERGE."""
+    pkg = _pkg()
+    plan, ref, n = make_pair((16, 16, 16), split=(2, 2, 1), t=2, seed=4, alpha=4.0)
+    with pytest.raises(pkg.MBSError) as ei:
+        plan.solve(torch.from_numpy(point_source(ref.shape)).cuda(), tol=1e-6, max_iter=2000)
+    assert ei.value.status == 6
+    plan.close()
+
+
+def test_budget_exhausted_returns_last_iterate():
+    plan, ref, n = make_pair((20, 16, 12), split=(2, 1, 2), t=3, seed=3)
+    src = point_source(ref.shape)
+    x, it, res = plan.solve(torch.from_numpy(src).cuda(), tol=1e-12, max_iter=17)
+    xr, itr, _ = ref.solve(src, tol=0.0, max_iter=17)
+    assert it == 17 and res > 1e-12
+    assert relative_l2(x.cpu().numpy(), xr) < ITER_TOL
+    plan.close()
+
+
+def test_out_of_memory_is_reported_without_allocating():
+    """A plan larger than the free device memory fails with MBS_ENOMEM before any
+    allocation (the refractive index is not read before the memory check)."""
+    import ctypes as C
+
+    pkg = _pkg()
+    lib = pkg.load_library()
+    dummy = torch.ones((1, 1, 1), dtype=torch.complex64, device="cuda")
+    opts = pkg._Options()
+    lib.mbs_default_options(C.byref(opts))
+    free0, _ = torch.cuda.mem_get_info()
+    h = C.c_void_p()
+    st = lib.mbs_plan_create(C.byref(h), (C.c_int64 * 3)(4096, 4096, 4096), 0.25, 1.0,
+                             C.c_void_p(dummy.data_ptr()), (C.c_int32 * 6)(8, 8, 8, 8, 8, 8),
+                             (C.c_int32 * 3)(8, 8, 8), C.byref(opts))
+    assert st == 2, lib.mbs_last_error()
+    assert not h.value
+    free1, _ = torch.cuda.mem_get_info()
+    assert abs(free1 - free0) < (64 << 20)
