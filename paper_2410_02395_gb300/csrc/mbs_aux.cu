@@ -510,9 +510,13 @@ __global__ void __launch_bounds__(256, 4) k_shell(const __grid_constant__ ShellA
     }
   }
   // (2) axis-2 layer positions of rows outside the axis-0/1 layers, flattened
+  // (32-bit index arithmetic while the flattened count fits: 64-bit division
+  // per voxel would dominate this loop)
   const long long nc1 = a.g.N1 - a.tb.nl1;
   const long long npart = (a.g.N0 - a.tb.nl0) * nc1 * a.tb.nsh2;
   const long long nth = (long long)gridDim.x * blockDim.x;
+  const bool narrow = npart < (1ll << 31);
+  const unsigned nsh2 = (unsigned)a.tb.nsh2, nc1u = (unsigned)nc1;
   for (long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; j0 < npart; j0 += nth * U) {
     long long v[U];
 #pragma unroll
@@ -520,8 +524,18 @@ __global__ void __launch_bounds__(256, 4) k_shell(const __grid_constant__ ShellA
       const long long j = j0 + nth * u;
       v[u] = -1;
       if (j < npart) {
-        const long long row = j / a.tb.nsh2, k = j - row * a.tb.nsh2;
-        const long long i0 = a.tb.c0[row / nc1], i1 = a.tb.c1[row - (row / nc1) * nc1];
+        long long i0, i1, k;
+        if (narrow) {
+          const unsigned ju = (unsigned)j, row = ju / nsh2, q = row / nc1u;
+          k = ju - row * nsh2;
+          i0 = a.tb.c0[q];
+          i1 = a.tb.c1[row - q * nc1u];
+        } else {
+          const long long row = j / a.tb.nsh2;
+          k = j - row * a.tb.nsh2;
+          i0 = a.tb.c0[row / nc1];
+          i1 = a.tb.c1[row - (row / nc1) * nc1];
+        }
         v[u] = (i0 * a.g.N1 + i1) * N2 + a.tb.sh2list[k];
       }
     }

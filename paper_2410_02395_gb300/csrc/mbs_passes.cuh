@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(32 * warps_for(N), MIN_BLOCKS) k_mid_turn(cons
     const float dx = fmaf(-c.x, p2, ck0.x), dy = fmaf(-c.y, p2, ck0.y);  // c (k0^2 - |p|^2)
     if (prop) {
       const float ex = dx + 1.f;
-      const float inv = m.sc / fmaf(ex, ex, dy * dy);
+      const float inv = m.sc * __frcp_rn(fmaf(ex, ex, dy * dy));
       return cmul(v, make_float2(ex * inv, -dy * inv));
     }
     return cmul(v, make_float2(dx * m.sc, dy * m.sc));
