@@ -75,6 +75,11 @@ def layer_fractions(info):
     return {"L": sum(fd), "L01": fd[0] + fd[1], "sh": sh, "g01": g01}
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel from one ncu capture of the current kernels (see profiles/).
+MEASURED_TRAFFIC = {("C2", "rows_first"): 419167232}
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -371,7 +376,7 @@ def main():
         bytes_per_launch = kernel_bytes_per_voxel(dom, fr) * vox / max(1.0, dom_launches / K)
         achieved = bytes_per_launch / (dom_ms / dom_launches / 1e3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": dom, "peak_source": peak_src,
+                    "traffic": MEASURED_TRAFFIC.get((args.workload, dom)), "kernel": dom, "peak_source": peak_src,
                     "share": prof[dom][1] / tot if tot else None,
                     "bytes_per_launch": bytes_per_launch,
                     "kernels": {k: {"launches": v[0], "ms_per_iter": v[1] / K,
