@@ -74,7 +74,8 @@ typedef enum mbs_operator {
 /* Limits of this build. */
 #define MBS_MAX_SPLIT 16 /* subdomains per axis */
 #define MBS_MAX_T 32     /* truncation width; compiled values t = 1..16, 20, 24, 32 */
-#define MBS_MAX_EDGE 512 /* longest subdomain edge; edges must factor into 2, 3, 5, 7 */
+#define MBS_MAX_EDGE 512 /* longest subdomain edge; every edge <= 512 whose prime factors are
+                            2, 3, 5 and 7 has compiled FFT kernels (106 lengths) */
 
 /* Option flags. */
 #define MBS_FLAG_NO_GRAPH (1u << 0)  /* launch kernels one by one instead of replaying a CUDA graph */

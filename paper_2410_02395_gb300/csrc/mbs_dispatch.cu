@@ -1,32 +1,30 @@
 // Dispatch of the FFT pass kernels by subdomain edge length.
+#include "mbs_fft_sizes.h"
 #include "mbs_internal.h"
 
 namespace mbs {
-bool fft_group_0(int, int, int, bool, const PassArgs&, int, cudaStream_t, cudaError_t*);
-bool fft_group_0_has(int);
-bool fft_group_1(int, int, int, bool, const PassArgs&, int, cudaStream_t, cudaError_t*);
-bool fft_group_1_has(int);
-bool fft_group_2(int, int, int, bool, const PassArgs&, int, cudaStream_t, cudaError_t*);
-bool fft_group_2_has(int);
-bool fft_group_3(int, int, int, bool, const PassArgs&, int, cudaStream_t, cudaError_t*);
-bool fft_group_3_has(int);
-bool fft_group_4(int, int, int, bool, const PassArgs&, int, cudaStream_t, cudaError_t*);
-bool fft_group_4_has(int);
-bool fft_group_5(int, int, int, bool, const PassArgs&, int, cudaStream_t, cudaError_t*);
-bool fft_group_5_has(int);
+#define MBS_DECLARE_GROUP(k)                                                                           \
+  bool fft_group_##k(int, int, int, bool, const PassArgs&, int, cudaStream_t, cudaError_t*);           \
+  bool fft_group_##k##_has(int);
+MBS_FFT_GROUP_IDS(MBS_DECLARE_GROUP)
+#undef MBS_DECLARE_GROUP
 
 static cudaError_t dispatch(int n, int kind, int axis, bool inv, const PassArgs& a, int nrb, cudaStream_t st) {
   cudaError_t err = cudaErrorInvalidValue;
-  if (fft_group_0(n, kind, axis, inv, a, nrb, st, &err)) return err;
-  if (fft_group_1(n, kind, axis, inv, a, nrb, st, &err)) return err;
-  if (fft_group_2(n, kind, axis, inv, a, nrb, st, &err)) return err;
-  if (fft_group_3(n, kind, axis, inv, a, nrb, st, &err)) return err;
-  if (fft_group_4(n, kind, axis, inv, a, nrb, st, &err)) return err;
-  if (fft_group_5(n, kind, axis, inv, a, nrb, st, &err)) return err;
+#define MBS_TRY_GROUP(k) \
+  if (fft_group_##k(n, kind, axis, inv, a, nrb, st, &err)) return err;
+  MBS_FFT_GROUP_IDS(MBS_TRY_GROUP)
+#undef MBS_TRY_GROUP
   return cudaErrorInvalidValue;
 }
 
-bool fft_size_compiled(int n) { return fft_group_0_has(n) || fft_group_1_has(n) || fft_group_2_has(n) || fft_group_3_has(n) || fft_group_4_has(n) || fft_group_5_has(n); }
+bool fft_size_compiled(int n) {
+#define MBS_HAS_GROUP(k) \
+  if (fft_group_##k##_has(n)) return true;
+  MBS_FFT_GROUP_IDS(MBS_HAS_GROUP)
+#undef MBS_HAS_GROUP
+  return false;
+}
 
 cudaError_t launch_rows_first(int n, const PassArgs& a, int nrb, cudaStream_t st) { return dispatch(n, 0, 2, false, a, nrb, st); }
 cudaError_t launch_rows_last(int n, const PassArgs& a, int nrb, cudaStream_t st) { return dispatch(n, 1, 2, true, a, nrb, st); }

@@ -1,0 +1,3 @@
+// FFT pass kernels for the subdomain edges of size group 13 (mbs_fft_sizes.h).
+#define MBS_FFT_GROUP 13
+#include "mbs_fft_group.cuh"

@@ -1,0 +1,3 @@
+// FFT pass kernels for the subdomain edges of size group 9 (mbs_fft_sizes.h).
+#define MBS_FFT_GROUP 9
+#include "mbs_fft_group.cuh"

@@ -621,8 +621,8 @@ cudaError_t run_size(int kind, int axis, bool inv, const PassArgs& a, int nrow_b
 
 }  // namespace mbs
 
-// Size-group translation units define
-//   bool mbs_fft_group_<k>(int n, int kind, int axis, bool inv, const PassArgs&, int, cudaStream_t, cudaError_t*)
+// One case of a size-group switch (mbs_fft_group.cuh): launch the pass kernel
+// for edge n and report its launch status through *err.
 #define MBS_CASE(n) \
   case n:           \
     *err = mbs::run_size<n>(kind, axis, inv, a, nrb, st); \

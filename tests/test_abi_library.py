@@ -64,3 +64,26 @@ def test_workspace_query_and_validation(lib):
     assert ei.value.status == 1
     with pytest.raises(pkg.MBSError):
         pkg.Plan.workspace_bytes((12, 8, 8), (2, 1, 1), split_sizes=[[5, 6], [8], [8]])
+
+
+def _smooth7(v):
+    for p in (2, 3, 5, 7):
+        while v % p == 0:
+            v //= p
+    return v == 1
+
+
+def test_every_7_smooth_edge_up_to_512_is_compiled(lib):
+    """The header's size rule: an edge <= 512 is accepted exactly when its prime
+    factors are 2, 3, 5 and 7; anything else is MBS_EUNSUPPORTED."""
+    import paper_2410_02395_gb300 as pkg
+
+    for n in range(1, 520):
+        ok = n <= 512 and _smooth7(n)
+        try:
+            pkg.Plan.workspace_bytes((8, 8, n), (1, 1, 1), truncation=1)
+            got = True
+        except pkg.MBSError as e:
+            assert e.status == 8, (n, e.status)
+            got = False
+        assert got == ok, n
