@@ -79,7 +79,13 @@ struct PassArgs {
   float alpha;
   const float2* cW;     // c * W (t x t) for the axis-2 corrections fused into the first pass
   int fuse_e2;          // 1: the first pass computes E_2 x itself; 0: E_2 x is in K with E_0 x, E_1 x
-  const float2* tw;     // twiddles exp(-2 pi i k / N), k < N
+  const float2* tw;     // twiddles exp(-2 pi i k / N), k < N (Bluestein lengths: of the M-point FFT)
+  // Bluestein lengths (an edge n with a prime factor above 7): the chirp
+  // exp(-i pi m^2 / n), m < n, and the M-point spectra of the conjugate chirp
+  // divided by M (forward transform: [0, M), inverse: [M, 2M)); null otherwise.
+  const float2* bl_chirp;
+  const float2* bl_bhat;
+  int bl_n;
   AxisTables tb;
   GridDesc g;
   double* partials;     // per-block FP64 partial sums of |r|^2 (null: none)
@@ -125,6 +131,7 @@ struct ShellArgs {
   double* hist;
   const DevState* state;
   int mode;
+  const float2* cW;     // c W (t x t), for the fused axis-2 corrections of launch_shell_rows
 };
 
 // Launchers (return cudaGetLastError of the launch).
@@ -132,11 +139,23 @@ cudaError_t launch_rows_first(int n, const PassArgs& a, int nrows_blocks, cudaSt
 cudaError_t launch_rows_last(int n, const PassArgs& a, int nrows_blocks, cudaStream_t st);
 cudaError_t launch_strided(int n, int axis, bool inv, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_mid(int n, const PassArgs& a, cudaStream_t st);
+// Bluestein FFT lengths: the M of the convolution for edge n (0: n has no
+// compiled Bluestein form), and the launcher the dispatch falls back to.
+int bluestein_len(int n);
+bool bluestein_launch(int n, int kind, int axis, bool inv, const PassArgs& a, int nrb, cudaStream_t st,
+                      cudaError_t* err);
 bool fft_size_compiled(int n);
 
 cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st);
 bool corr_t_supported(int t);
 cudaError_t launch_shell(const ShellArgs& a, int blocks, cudaStream_t st);
+// The layer update of the iteration (SHELL_UPDATE_ITER / SHELL_UPDATE_RES) with
+// the axis-2 corrections of e computed in the same kernel (C then holds only the
+// axis-0/1 terms). shell_rows_supported says whether the plan's t and axis-2
+// split fit it; otherwise the caller runs the axis-2 correction kernel and
+// launch_shell.
+bool shell_rows_supported(const GridDesc& g);
+cudaError_t launch_shell_rows(const ShellArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_state_arm(DevState* state, int add_iter, double tol, int reset, int hist_cap, cudaStream_t st);
 
 // Plan set-up kernels (FP64 arithmetic on the device).

@@ -163,9 +163,12 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
   const int off2 = a.g.ax[2].off[j2];
   const RowTile rt = setup_rows(masks, a, off2);
   const bool iter = a.mode == FIRST_ITER;
-  const float2* __restrict__ X = a.X;
-  const float2* __restrict__ B = a.B;
-  float2* K = a.K;
+  // The tile's 32 rows x N elements lie within 32 * N2 <= 2^18 voxels of its
+  // origin, so in-tile offsets are 32-bit.
+  const float2* __restrict__ Xt = a.X + rt.base0;
+  const float2* __restrict__ Bt = a.B + rt.base0;
+  float2* Kt = a.K + rt.base0;
+  const unsigned n2 = (unsigned)a.g.N2;
   // Axis-2 edge corrections of x on this segment (Sec. 3.1 steps 1-5) need the
   // segment's own first/last t voxels and the neighbours' adjacent t voxels of
   // every row: fetched asynchronously into shared memory while the tile loads.
@@ -173,11 +176,14 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
   const int t = TC > 0 ? TC : a.g.t;
   const AxisDesc& ax2 = a.g.ax[2];
   const int L = ax2.left[j2], R = ax2.right[j2];
-  float2* xe = dyn + N * kPad;         // [32 rows][4t]: own first t, own last t, left's last t, right's first t
-  float2* wsm = xe + 32 * 4 * t;       // Toeplitz weights cw[m] = cW at column - row = m - (t - 1)
+  // xe[k][r] (pitch 33): k < t own first t, < 2t own last t, < 3t left's last t,
+  // < 4t right's first t of row r. c is purely imaginary and W real, so cW = i w
+  // with w = Im(cW) real: wsm[m] = w at column - row = m - (t - 1).
+  float2* xe = dyn + N * kPad;
+  float* wsm = reinterpret_cast<float*>(xe + 4 * t * kPad);
   if (e2) {
     for (int idx = tid; idx < 32 * 4 * t; idx += NT) {
-      const int r = idx / (4 * t), k = idx - r * 4 * t;
+      const int r = idx / (4 * t), k = idx - r * 4 * t;  // consecutive threads: one row's values
       long long pos = -1;
       if (rt.ok(r)) {
         if (k < t) pos = off2 + k;
@@ -185,13 +191,13 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
         else if (k < 3 * t) pos = L >= 0 ? ax2.off[L] + ax2.n[L] - t + (k - 2 * t) : -1;
         else pos = R >= 0 ? ax2.off[R] + (k - 3 * t) : -1;
       }
-      if (pos >= 0) cp_async8(xe + idx, X + (rt.base(r) - off2) + pos);
-      else xe[idx] = make_float2(0.f, 0.f);
+      if (pos >= 0) cp_async8(xe + k * kPad + r, Xt + ((long long)r * n2 + (pos - off2)));
+      else xe[k * kPad + r] = make_float2(0.f, 0.f);
     }
     cp_async_commit();
     if (tid < 2 * t - 1) {
       const int m = tid, aa = m < t - 1 ? t - 1 - m : 0, bb = aa + m - (t - 1);
-      wsm[m] = a.cW[aa * t + bb];
+      wsm[m] = a.cW[aa * t + bb].y;
     }
   }
   for (int k0 = 0; k0 < PERT; k0 += CH) {
@@ -202,11 +208,11 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
       const bool ok = TileMap<N, NT>::at(tid, k0 + c, r, e);
       xv[c] = bv[c] = cv[c] = make_float2(0.f, 0.f);
       if (ok && rt.ok(r)) {
-        const long long gi = rt.base(r) + e;
-        xv[c] = __ldg(X + gi);
+        const unsigned o = (unsigned)r * n2 + (unsigned)e;
+        xv[c] = __ldg(Xt + o);
         if (iter) {
-          bv[c] = __ldg(B + gi);
-          if (rt.lay(r) || (!a.fuse_e2 && in_layer2<N>(a, e))) cv[c] = K[gi];  // E x from the correction kernels
+          bv[c] = __ldg(Bt + o);
+          if (rt.lay(r) || (!a.fuse_e2 && in_layer2<N>(a, e))) cv[c] = Kt[o];  // E x from the correction kernels
         }
       }
     }
@@ -225,36 +231,60 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
     }
   }
   if (e2) {
+    // Warp w corrects tile elements q(k) for k = w, w + W, ... < 2t, lane = row:
     //   first t: u -= sum_b cW[b][q]  (x_left[n_l-t+b] - x[n-t+b])
     //   last t:  u -= sum_b cW[aa][b] (x_right[b]      - x[b])
+    // with cW = i w: sum_b cW d_b = i v, v = sum_b w_b d_b.
     cp_async_wait_all();
     __syncthreads();
-    for (int idx = tid; idx < 32 * 2 * t; idx += NT) {
-      const int r = idx / (2 * t), k = idx - r * 2 * t;
+    for (int k = warp; k < 2 * t; k += W) {
       const int q = k < t ? k : N - t + (k - t);
       if (k >= t && q < t) continue;  // also in the first range (N < 2t): done there
-      const float2* x4 = xe + r * 4 * t;
-      float2 v = make_float2(0.f, 0.f);
+      const float2* xr = xe + lane;
+      float vx = 0.f, vy = 0.f;
       if constexpr (TC > 0) {
         if (q < TC) {
 #pragma unroll
-          for (int b = 0; b < TC; b++) v = cadd(v, cmul(wsm[q - b + TC - 1], csub(x4[2 * TC + b], x4[TC + b])));
+          for (int b = 0; b < TC; b++) {
+            const float w = wsm[q - b + TC - 1];
+            const float2 d = csub(xr[(2 * TC + b) * kPad], xr[(TC + b) * kPad]);
+            vx = fmaf(w, d.x, vx);
+            vy = fmaf(w, d.y, vy);
+          }
         }
         if (q >= N - TC) {
           const int aa = q - (N - TC);
 #pragma unroll
-          for (int b = 0; b < TC; b++) v = cadd(v, cmul(wsm[b - aa + TC - 1], csub(x4[3 * TC + b], x4[b])));
+          for (int b = 0; b < TC; b++) {
+            const float w = wsm[b - aa + TC - 1];
+            const float2 d = csub(xr[(3 * TC + b) * kPad], xr[b * kPad]);
+            vx = fmaf(w, d.x, vx);
+            vy = fmaf(w, d.y, vy);
+          }
         }
       } else {
         if (q < t) {
-          for (int b = 0; b < t; b++) v = cadd(v, cmul(wsm[q - b + t - 1], csub(x4[2 * t + b], x4[t + b])));
+          for (int b = 0; b < t; b++) {
+            const float w = wsm[q - b + t - 1];
+            const float2 d = csub(xr[(2 * t + b) * kPad], xr[(t + b) * kPad]);
+            vx = fmaf(w, d.x, vx);
+            vy = fmaf(w, d.y, vy);
+          }
         }
         if (q >= N - t) {
           const int aa = q - (N - t);
-          for (int b = 0; b < t; b++) v = cadd(v, cmul(wsm[b - aa + t - 1], csub(x4[3 * t + b], x4[b])));
+          for (int b = 0; b < t; b++) {
+            const float w = wsm[b - aa + t - 1];
+            const float2 d = csub(xr[(3 * t + b) * kPad], xr[b * kPad]);
+            vx = fmaf(w, d.x, vx);
+            vy = fmaf(w, d.y, vy);
+          }
         }
       }
-      sm[q][r] = csub(sm[q][r], v);
+      float2 u = sm[q][lane];
+      u.x += vy;  // u -= i v
+      u.y -= vx;
+      sm[q][lane] = u;
     }
   }
   if constexpr (N > 1) {
@@ -266,7 +296,7 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
   __syncthreads();
   for (int k0 = 0; k0 < PERT; k0++) {
     int r, e;
-    if (TileMap<N, NT>::at(tid, k0, r, e) && rt.ok(r)) K[rt.base(r) + e] = sm[e][r];
+    if (TileMap<N, NT>::at(tid, k0, r, e) && rt.ok(r)) Kt[(unsigned)r * n2 + (unsigned)e] = sm[e][r];
   }
 }
 
@@ -550,9 +580,9 @@ cudaError_t run_size(int kind, int axis, bool inv, const PassArgs& a, int nrow_b
   const unsigned gx = (unsigned)((a.g.N2 + 31) / 32);
   switch (kind) {
     case 0: {
-      // tile, then the axis-2 edge values [32][4t] and the 2t-1 Toeplitz weights
-      const size_t edge = a.g.ax[2].a > 0 ? ((size_t)32 * 4 * a.g.t + 2 * a.g.t) * sizeof(float2) : 0;
-      const size_t smax = sm + ((size_t)32 * 4 * kMaxT + 2 * kMaxT) * sizeof(float2);
+      // tile, then the axis-2 edge values [4t][33] and the 2t-1 Toeplitz weights (floats)
+      const size_t edge = a.g.ax[2].a > 0 ? ((size_t)4 * a.g.t * kPad + a.g.t) * sizeof(float2) : 0;
+      const size_t smax = sm + ((size_t)4 * kMaxT * kPad + kMaxT) * sizeof(float2);
       if (a.g.t == 8) {
         e = set_smem(k_rows_first<N, 8>, smax);
         if (e) return e;
