@@ -55,7 +55,7 @@ typedef enum mbs_status {
   MBS_ENAN = 5,        /* residual became NaN or Inf */
   MBS_EDIVERGE = 6,    /* residual kept rising (the iteration is monotone in exact arithmetic, Sec. 2) */
   MBS_ETIMEOUT = 7,    /* a bounded device wait expired */
-  MBS_EUNSUPPORTED = 8 /* size outside the compiled FFT lengths or limits below */
+  MBS_EUNSUPPORTED = 8 /* size outside the supported FFT lengths or limits below */
 } mbs_status;
 
 /* Operators for mbs_apply_operator (all act on the whole decomposed grid). */
@@ -74,8 +74,9 @@ typedef enum mbs_operator {
 /* Limits of this build. */
 #define MBS_MAX_SPLIT 16 /* subdomains per axis */
 #define MBS_MAX_T 32     /* truncation width; compiled values t = 1..16, 20, 24, 32 */
-#define MBS_MAX_EDGE 512 /* longest subdomain edge; every edge <= 512 whose prime factors are
-                            2, 3, 5 and 7 has compiled FFT kernels (106 lengths) */
+#define MBS_MAX_EDGE 512 /* longest subdomain edge. Edges <= 512 whose prime factors are 2, 3,
+                            5 and 7 have mixed-radix FFT kernels (106 lengths); any other edge
+                            <= 256 is transformed by Bluestein's algorithm on one of them */
 
 /* Option flags. */
 #define MBS_FLAG_NO_GRAPH (1u << 0)  /* launch kernels one by one instead of replaying a CUDA graph */
@@ -122,8 +123,8 @@ MBS_API void mbs_default_options(mbs_options *opts);
  * medium factor B = 1 - c (k^2 - k0^2) stored as complex64.
  * Errors: MBS_EINVAL (shape < 1, split not in [1, MBS_MAX_SPLIT], t < 0 or
  * > MBS_MAX_T, t larger than a subdomain edge on a corrected axis, non-finite n,
- * wavelength or pixel size <= 0), MBS_EUNSUPPORTED (an edge not a compiled FFT
- * length), MBS_ENOMEM (buffers do not fit; nothing is allocated), MBS_ECUDA.
+ * wavelength or pixel size <= 0), MBS_EUNSUPPORTED (an edge outside the FFT
+ * lengths of MBS_MAX_EDGE), MBS_ENOMEM (buffers do not fit; nothing is allocated), MBS_ECUDA.
  */
 MBS_API mbs_status mbs_plan_create(mbs_plan **plan, const int64_t shape[3], double pixel_size, double wavelength,
                            const void *refractive_index, const int32_t boundary_widths[6],

@@ -136,6 +136,9 @@ struct mbs_plan {
   int nsh2;
   float2* cW;
   std::map<int, float2*> tw;
+  // Bluestein edges (a prime factor above 7): chirp (n) and spectra (2M) per edge
+  std::map<int, float2*> bl_chirp, bl_bhat;
+  bool bl_axis2;  // an axis-2 edge is a Bluestein length (no fused axis-2 corrections then)
   double* partials;
   int n_rows_partials, n_shell_partials;
   DevState* state;
@@ -207,10 +210,17 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
   char* plc0 = take(p->N[0] * sizeof(int));
   char* plc1 = take(p->N[1] * sizeof(int));
   char* pcw = take(std::max(1, p->t * p->t) * sizeof(float2));
-  std::map<int, char*> ptw;
+  std::map<int, char*> ptw, pchirp, pbhat;
   for (int d = 0; d < 3; d++)
-    for (auto& gsz : p->groups[d])
-      if (!ptw.count(gsz.n)) ptw[gsz.n] = take(gsz.n * sizeof(float2));
+    for (auto& gsz : p->groups[d]) {
+      const int n = gsz.n;
+      const int tl = fft_size_compiled(n) ? n : bluestein_len(n);
+      if (!ptw.count(tl)) ptw[tl] = take(tl * sizeof(float2));
+      if (tl != n && !pchirp.count(n)) {
+        pchirp[n] = take(n * sizeof(float2));
+        pbhat[n] = take(2 * tl * sizeof(float2));
+      }
+    }
   const int64_t rows = p->N[0] * p->N[1];
   const int nrb = (int)((rows + 31) / 32);
   const int nrows_partials = nrb * p->S[2];
@@ -242,6 +252,13 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
     p->cW = (float2*)pcw;
     p->tw.clear();
     for (auto& kv : ptw) p->tw[kv.first] = (float2*)kv.second;
+    p->bl_chirp.clear();
+    p->bl_bhat.clear();
+    for (auto& kv : pchirp) p->bl_chirp[kv.first] = (float2*)kv.second;
+    for (auto& kv : pbhat) p->bl_bhat[kv.first] = (float2*)kv.second;
+    p->bl_axis2 = false;
+    for (auto& gz : p->groups[2])
+      if (!fft_size_compiled(gz.n)) p->bl_axis2 = true;
     p->partials = (double*)ppart;
     p->n_rows_partials = nrows_partials;
     p->n_shell_partials = kShellBlocks;
@@ -300,9 +317,9 @@ mbs_status validate_and_fill(mbs_plan* p, const int64_t shape[3], double h, doub
     p->a[d] = (split[d] == 1 && per) ? 0 : (split[d] == 1 ? 1 : 2);
     for (int s = 0; s < split[d]; s++) {
       const int n = p->sizes[d][s];
-      if (n > kMaxFFT || !fft_size_compiled(n))
+      if (n > kMaxFFT || !(fft_size_compiled(n) || bluestein_len(n) > 0))
         return fail(MBS_EUNSUPPORTED, "subdomain edge " + std::to_string(n) +
-                                          " is not a compiled FFT length (2^a 3^b 5^c 7^d list, <= 512)");
+                                          " has no FFT (2^a 3^b 5^c 7^d up to 512, any other length up to 256)");
       if (p->a[d] > 0 && p->t > n) return fail(MBS_EINVAL, "truncation t exceeds a subdomain edge");
       if ((p->flags & MBS_FLAG_CORR_TF32) && p->a[d] > 0 && 2 * p->t > n)
         return fail(MBS_EUNSUPPORTED, "tensor-core corrections need subdomain edges >= 2t");
@@ -400,6 +417,46 @@ mbs_status upload_tables(mbs_plan* p) {
     CU(cudaMemcpyAsync(kv.second, w.data(), n * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
     CU(cudaStreamSynchronize(p->stream));
   }
+  // Bluestein tables in FP64: chirp c[m] = exp(-i pi m^2 / n) (m^2 reduced mod 2n),
+  // b[m] = conj(c[|m|]) for |m| < n (indices mod M), spectra FFT_M(b) / M and
+  // FFT_M(conj b) / M by the direct DFT (M <= 512).
+  for (auto& kv : p->bl_chirp) {
+    const int n = kv.first, M = bluestein_len(n);
+    std::vector<double> cr(n), ci(n);
+    for (int m = 0; m < n; m++) {
+      const long long q = ((long long)m * m) % (2LL * n);
+      const double ang = -M_PI * (double)q / n;
+      cr[m] = cos(ang);
+      ci[m] = sin(ang);
+    }
+    std::vector<double> br(M, 0.0), bi(M, 0.0);
+    for (int m = 0; m < n; m++) {
+      br[m] = cr[m];
+      bi[m] = -ci[m];
+      if (m > 0) {
+        br[M - m] = cr[m];
+        bi[M - m] = -ci[m];
+      }
+    }
+    std::vector<float2> chirp(n), bhat(2 * M);
+    for (int m = 0; m < n; m++) chirp[m] = make_float2((float)cr[m], (float)ci[m]);
+    for (int k = 0; k < M; k++) {
+      double fr = 0, fi = 0, gr = 0, gi = 0;  // FFT_M(b)[k], FFT_M(conj b)[k]
+      for (int m = 0; m < M; m++) {
+        const long long q = ((long long)m * k) % M;
+        const double ang = -2.0 * M_PI * (double)q / M, wr = cos(ang), wi = sin(ang);
+        fr += br[m] * wr - bi[m] * wi;
+        fi += br[m] * wi + bi[m] * wr;
+        gr += br[m] * wr + bi[m] * wi;
+        gi += br[m] * wi - bi[m] * wr;
+      }
+      bhat[k] = make_float2((float)(fr / M), (float)(fi / M));
+      bhat[M + k] = make_float2((float)(gr / M), (float)(gi / M));
+    }
+    CU(cudaMemcpyAsync(kv.second, chirp.data(), n * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    CU(cudaMemcpyAsync(p->bl_bhat[n], bhat.data(), 2 * M * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+  }
   AxisTables& tb = p->tb;
   for (int d = 0; d < 3; d++) {
     tb.p2[d] = p->p2[d];
@@ -462,6 +519,25 @@ mbs_status setup_medium(mbs_plan* p, const float2* n_dev) {
   return MBS_OK;
 }
 
+// The first pass computes the axis-2 corrections of x itself unless they run on
+// the tensor cores or an axis-2 edge takes the Bluestein kernels.
+bool fuse_e2(const mbs_plan* p) { return !(p->flags & MBS_FLAG_CORR_TF32) && !p->bl_axis2; }
+
+// Twiddles (and Bluestein tables) of the transform of edge n.
+void set_len_tables(const mbs_plan* p, PassArgs& a, int n) {
+  if (fft_size_compiled(n)) {
+    a.tw = p->tw.at(n);
+    a.bl_chirp = nullptr;
+    a.bl_bhat = nullptr;
+    a.bl_n = 0;
+  } else {
+    a.tw = p->tw.at(bluestein_len(n));
+    a.bl_chirp = p->bl_chirp.at(n);
+    a.bl_bhat = p->bl_bhat.at(n);
+    a.bl_n = n;
+  }
+}
+
 PassArgs base_args(mbs_plan* p) {
   PassArgs a;
   memset(&a, 0, sizeof(a));
@@ -475,7 +551,7 @@ PassArgs base_args(mbs_plan* p) {
   a.mc = make_float2((float)-p->c_re, (float)-p->c_im);
   a.alpha = (float)p->alpha;
   a.cW = p->cW;
-  a.fuse_e2 = (p->flags & MBS_FLAG_CORR_TF32) ? 0 : 1;
+  a.fuse_e2 = fuse_e2(p) ? 1 : 0;
   a.tb = p->tb;
   a.g = p->g;
   return a;
@@ -491,7 +567,15 @@ ShellArgs shell_args(mbs_plan* p) {
   s.alpha = (float)p->alpha;
   s.tb = p->tb;
   s.g = p->g;
+  s.cW = p->cW;
   return s;
+}
+
+// The iteration's layer update computes the axis-2 corrections of e itself
+// (one launch and one pass over the axis-2 layers less) unless the corrections
+// run on the tensor cores or the axis-2 split has too many layer voxels per row.
+bool fused_layer_update(const mbs_plan* p) {
+  return !(p->flags & MBS_FLAG_CORR_TF32) && shell_rows_supported(p->g);
 }
 
 // Edge corrections E F into the buffer C at the boundary-layer voxels.
@@ -558,7 +642,7 @@ cudaError_t run_transform_chain(mbs_plan* p, PassArgs a, int first_mode, int mid
   for (auto& gz : p->groups[2]) {
     a.nsub = gz.nsub;
     memcpy(a.subs, gz.subs, sizeof(a.subs));
-    a.tw = p->tw[gz.n];
+    set_len_tables(p, a, gz.n);
     if (rec) rec->begin(KK_ROWS_FIRST);
     e = launch_rows_first(gz.n, a, nrb, p->stream);
     if (rec) rec->end();
@@ -568,7 +652,7 @@ cudaError_t run_transform_chain(mbs_plan* p, PassArgs a, int first_mode, int mid
     if (gy.n == 1) continue;
     a.nsub = gy.nsub;
     memcpy(a.subs, gy.subs, sizeof(a.subs));
-    a.tw = p->tw[gy.n];
+    set_len_tables(p, a, gy.n);
     if (rec) rec->begin(KK_STRIDED_FWD);
     e = launch_strided(gy.n, 1, false, a, p->stream);
     if (rec) rec->end();
@@ -578,7 +662,7 @@ cudaError_t run_transform_chain(mbs_plan* p, PassArgs a, int first_mode, int mid
   for (auto& gx : p->groups[0]) {
     a.nsub = gx.nsub;
     memcpy(a.subs, gx.subs, sizeof(a.subs));
-    a.tw = p->tw[gx.n];
+    set_len_tables(p, a, gx.n);
     if (rec) rec->begin(KK_MID);
     e = launch_mid(gx.n, a, p->stream);
     if (rec) rec->end();
@@ -589,7 +673,7 @@ cudaError_t run_transform_chain(mbs_plan* p, PassArgs a, int first_mode, int mid
     if (gy.n == 1) continue;
     a.nsub = gy.nsub;
     memcpy(a.subs, gy.subs, sizeof(a.subs));
-    a.tw = p->tw[gy.n];
+    set_len_tables(p, a, gy.n);
     if (rec) rec->begin(KK_STRIDED_INV);
     e = launch_strided(gy.n, 1, true, a, p->stream);
     if (rec) rec->end();
@@ -607,7 +691,7 @@ cudaError_t run_rows_last(mbs_plan* p, PassArgs a, int mode, bool partials, Reco
     auto& gz = p->groups[2][gi];
     a.nsub = gz.nsub;
     memcpy(a.subs, gz.subs, sizeof(a.subs));
-    a.tw = p->tw[gz.n];
+    set_len_tables(p, a, gz.n);
     a.partials = partials ? p->partials : nullptr;
     a.slot0 = poff;
     a.n_total = p->n_rows_partials + (p->has_shell ? kShellBlocks : 0);
@@ -635,7 +719,7 @@ cudaError_t enqueue_iteration_res(mbs_plan* p, Recorder* rec) {
   a.Xlo = p->xlo;
   a.state = p->state;
   if (p->has_shell) {
-    e = run_corr_rec(p, p->r, p->K, p->state, rec, KK_CORR_X, false);
+    e = run_corr_rec(p, p->r, p->K, p->state, rec, KK_CORR_X, !fuse_e2(p));
     if (e) return e;
   }
   e = run_transform_chain(p, a, FIRST_ITER, MID_PROP, rec);
@@ -643,7 +727,8 @@ cudaError_t enqueue_iteration_res(mbs_plan* p, Recorder* rec) {
   e = run_rows_last(p, a, LAST_RES, true, rec, !p->has_shell);
   if (e) return e;
   if (p->has_shell) {
-    e = run_corr_rec(p, p->ebuf, p->K, p->state, rec, KK_CORR_E, true);
+    const bool fused = fused_layer_update(p);
+    e = run_corr_rec(p, p->ebuf, p->K, p->state, rec, KK_CORR_E, !fused);
     if (e) return e;
     ShellArgs s = shell_args(p);
     s.X = p->r;
@@ -655,7 +740,7 @@ cudaError_t enqueue_iteration_res(mbs_plan* p, Recorder* rec) {
     s.fin = p->state;
     s.hist = p->history;
     if (rec) rec->begin(KK_SHELL_UPDATE);
-    e = launch_shell(s, kShellBlocks, p->stream);
+    e = fused ? launch_shell_rows(s, kShellBlocks, p->stream) : launch_shell(s, kShellBlocks, p->stream);
     if (rec) rec->end();
     if (e) return e;
   }
@@ -675,7 +760,7 @@ cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
     for (int i = 0; i < 6; i++) a.sbox[i] = p->sbox[i];
   }
   if (p->has_shell) {  // V #1: E_0 x + E_1 x on the boundary layers, into the FFT buffer (steps 1-2)
-    e = run_corr_rec(p, p->x, p->K, p->state, rec, KK_CORR_X, false);
+    e = run_corr_rec(p, p->x, p->K, p->state, rec, KK_CORR_X, !fuse_e2(p));
     if (e) return e;
   }
   e = run_transform_chain(p, a, FIRST_ITER, MID_PROP, rec);  // E_2 x inside the first pass
@@ -683,7 +768,8 @@ cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
   e = run_rows_last(p, a, LAST_ITER, true, rec, !p->has_shell);
   if (e) return e;
   if (p->has_shell) {  // V #2 on e = x - w: E e into the (now free) FFT buffer, then the layers' update
-    e = run_corr_rec(p, p->ebuf, p->K, p->state, rec, KK_CORR_E, true);
+    const bool fused = fused_layer_update(p);  // E_2 e inside the layer update
+    e = run_corr_rec(p, p->ebuf, p->K, p->state, rec, KK_CORR_E, !fused);
     if (e) return e;
     ShellArgs s = shell_args(p);
     s.state = p->state;
@@ -694,7 +780,7 @@ cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
     s.fin = p->state;
     s.hist = p->history;
     if (rec) rec->begin(KK_SHELL_UPDATE);
-    e = launch_shell(s, kShellBlocks, p->stream);
+    e = fused ? launch_shell_rows(s, kShellBlocks, p->stream) : launch_shell(s, kShellBlocks, p->stream);
     if (rec) rec->end();
     if (e) return e;
   }
@@ -929,7 +1015,7 @@ mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* o
         a.S = p->src;
         for (int i = 0; i < 6; i++) a.sbox[i] = p->sbox[i];
       }
-      if (p->has_shell) e = run_corr(p, xd, p->K, p->free_state, false);
+      if (p->has_shell) e = run_corr(p, xd, p->K, p->free_state, !fuse_e2(p));
       if (!e) e = run_transform_chain(p, a, FIRST_ITER, MID_PROP, nullptr);
       if (!e) e = run_rows_last(p, a, LAST_PRECOND, false, nullptr);
       if (!e && p->has_shell) {
@@ -973,14 +1059,14 @@ mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* o
         if (e) break;
         a.nsub = gx.nsub;
         memcpy(a.subs, gx.subs, sizeof(a.subs));
-        a.tw = p->tw[gx.n];
+        set_len_tables(p, a, gx.n);
         e = launch_mid(gx.n, a, p->stream);
       }
       for (auto& gy : p->groups[1]) {
         if (e || gy.n == 1) continue;
         a.nsub = gy.nsub;
         memcpy(a.subs, gy.subs, sizeof(a.subs));
-        a.tw = p->tw[gy.n];
+        set_len_tables(p, a, gy.n);
         e = launch_strided(gy.n, 1, true, a, p->stream);
       }
       if (!e) e = run_rows_last(p, a, LAST_PLAIN, false, nullptr);

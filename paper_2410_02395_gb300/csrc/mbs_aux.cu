@@ -547,6 +547,222 @@ __global__ void __launch_bounds__(256, 4) k_shell(const __grid_constant__ ShellA
   }
 }
 
+// Layer update with the axis-2 corrections fused in (SHELL_UPDATE_ITER or
+// SHELL_UPDATE_RES), in two independent parts of one launch:
+//   (a) rows inside an axis-0/1 layer, their voxels outside the axis-2 layers:
+//       E e = C (the axis-0/1 terms), warp per row, U voxels per lane in flight;
+//   (b) the axis-2 layer voxels of every row ("slots": per subdomain s its
+//       first t, then its last t voxels; M = 2tS <= 32 J, J per lane), warp per
+//       pair of rows: all loads of both rows are issued first (e, B, x and, on
+//       rows inside an axis-0/1 layer, C), e is staged in shared memory, then
+//       each slot's axis-2 correction (Sec. 3.1 steps 1-5, the formulas of
+//       k_corr_rows) gives E e = C + E_2 e and the update.
+// c is purely imaginary and W real: c W = i w with w = Im(c W), so
+// sum_b cW_b f_b = i v with v = sum_b w_b f_b.
+constexpr int kShellRowsMaxSlots = 64;
+
+template <int TC>
+__device__ __forceinline__ float2 axis2_corr_sum(const float* w, int t, int q, int n, const float2* own,
+                                                 const float2* nbl, const float2* nbr) {
+  float vx = 0.f, vy = 0.f;
+  const int T = TC > 0 ? TC : t;
+  if (q < T) {  // first t layers: row q of W^T on (left's last t - own last t)
+#pragma unroll (TC > 0 ? TC : 1)
+    for (int b = 0; b < T; b++) {
+      float2 f = make_float2(-own[T + b].x, -own[T + b].y);
+      if (nbl) f = cadd(f, nbl[b]);
+      vx = fmaf(w[q - b + T - 1], f.x, vx);
+      vy = fmaf(w[q - b + T - 1], f.y, vy);
+    }
+  }
+  if (q >= n - T) {  // last t layers: row q-(n-t) of W on (right's first t - own first t)
+    const int aa = q - (n - T);
+#pragma unroll (TC > 0 ? TC : 1)
+    for (int b = 0; b < T; b++) {
+      float2 f = make_float2(-own[b].x, -own[b].y);
+      if (nbr) f = cadd(f, nbr[b]);
+      vx = fmaf(w[b - aa + T - 1], f.x, vx);
+      vy = fmaf(w[b - aa + T - 1], f.y, vy);
+    }
+  }
+  return make_float2(-vy, vx);  // i v
+}
+
+template <int MODE>
+__device__ __forceinline__ float2 layer_step(float2 b, float2 e, float2 corr, float2 x, float alpha, float& racc) {
+  const float2 r = csub(cmul(b, e), corr);
+  if (MODE == SHELL_UPDATE_ITER) racc = fmaf(r.x, r.x, fmaf(r.y, r.y, racc));
+  return make_float2(fmaf(-alpha, r.x, x.x), fmaf(-alpha, r.y, x.y));
+}
+
+template <int MODE, int TC, int J>
+__global__ void __launch_bounds__(256, J == 1 ? 4 : 3) k_shell_rows(const __grid_constant__ ShellArgs a) {
+  extern __shared__ float2 ws[];  // [8 warps][2 rows][M] staged e
+  __shared__ double red[8];
+  __shared__ float w[2 * kMaxT];  // w[m] = Im(c W) at column - row = m - (t - 1)
+  if (a.state && a.state->done) return;
+  constexpr int U = 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = TC > 0 ? TC : a.g.t;
+  const AxisDesc& ax = a.g.ax[2];
+  const int M = (ax.a > 0 && t > 0) ? 2 * t * ax.S : 0;
+  if (threadIdx.x < 2 * t - 1) {
+    const int m = threadIdx.x, aa = m < t - 1 ? t - 1 - m : 0, bb = aa + m - (t - 1);
+    w[m] = a.cW[aa * t + bb].y;
+  }
+  __syncthreads();
+  const unsigned N1 = (unsigned)a.g.N1;
+  const unsigned n2 = (unsigned)a.g.N2;
+  const unsigned char* __restrict__ sh2 = a.tb.shell[2];
+  double acc = 0.0;
+  // (a) rows inside an axis-0/1 layer, voxels outside the axis-2 layers
+  {
+    const unsigned nl0 = (unsigned)a.tb.nl0, nl1 = (unsigned)a.tb.nl1;
+    const unsigned f0 = nl0 * N1;
+    const unsigned nfull = f0 + ((unsigned)a.g.N0 - nl0) * nl1;
+    for (unsigned fr = blockIdx.x * 8u + warp; fr < nfull; fr += gridDim.x * 8u) {
+      unsigned i0, i1;
+      if (fr < f0) {
+        i0 = (unsigned)a.tb.l0[fr / N1];
+        i1 = fr - (fr / N1) * N1;
+      } else {
+        const unsigned q = fr - f0;
+        i0 = (unsigned)a.tb.c0[q / nl1];
+        i1 = (unsigned)a.tb.l1[q - (q / nl1) * nl1];
+      }
+      const long long rb = ((long long)i0 * N1 + i1) * (long long)n2;
+      const float2* Cr = a.C + rb;
+      const float2* Er = a.E + rb;
+      const float2* __restrict__ Br = a.B + rb;
+      float2* Xr = a.X + rb;
+      for (unsigned k0 = lane; k0 < n2; k0 += 32 * U) {
+        float2 e[U], c[U], b[U], x[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const unsigned k = k0 + 32 * u;
+          ok[u] = k < n2 && !sh2[k];
+          if (ok[u]) {
+            c[u] = Cr[k];
+            e[u] = Er[k];
+            b[u] = __ldg(Br + k);
+            x[u] = Xr[k];
+          }
+        }
+        float r2 = 0.f;
+#pragma unroll
+        for (int u = 0; u < U; u++)
+          if (ok[u]) Xr[k0 + 32 * u] = layer_step<MODE>(b[u], e[u], c[u], x[u], a.alpha, r2);
+        acc += (double)r2;
+      }
+    }
+  }
+  // (b) the axis-2 layer voxels of every row, with their axis-2 corrections
+  if (M > 0) {
+    float2* evw = ws + warp * 2 * M;
+    int sj[J], qj[J];
+    bool use[J];
+#pragma unroll
+    for (int j = 0; j < J; j++) {
+      const int idx = lane + 32 * j;
+      use[j] = idx < M;
+      sj[j] = use[j] ? idx / (2 * t) : 0;
+      const int k = idx - sj[j] * 2 * t, n = ax.n[sj[j]];
+      qj[j] = k < t ? k : n - t + (k - t);
+      if (k >= t && qj[j] < t) use[j] = false;  // n < 2t: the voxel is the first-range slot q (still staged)
+    }
+    const unsigned rows = (unsigned)(a.g.N0 * a.g.N1);
+    const unsigned step = gridDim.x * 8u;
+    for (unsigned rho0 = blockIdx.x * 8u + warp; rho0 < rows; rho0 += 2 * step) {
+      const unsigned rho1 = rho0 + step;
+      const bool live1 = rho1 < rows;
+      const unsigned i00 = rho0 / N1, i10 = rho0 - i00 * N1;
+      const unsigned i01 = live1 ? rho1 / N1 : 0, i11 = live1 ? rho1 - i01 * N1 : 0;
+      const bool full0 = a.tb.shell[0][i00] | a.tb.shell[1][i10];
+      const bool full1 = live1 && (a.tb.shell[0][i01] | a.tb.shell[1][i11]);
+      const long long rb0 = (long long)rho0 * n2, rb1 = (long long)rho1 * n2;
+      float2 e0[J], b0[J], x0[J], c0[J], e1[J], b1[J], x1[J], c1[J];
+#pragma unroll
+      for (int j = 0; j < J; j++) {
+        if (lane + 32 * j < M) {
+          const long long o = ax.off[sj[j]] + qj[j];
+          e0[j] = a.E[rb0 + o];
+          b0[j] = __ldg(a.B + rb0 + o);
+          x0[j] = a.X[rb0 + o];
+          c0[j] = full0 ? a.C[rb0 + o] : make_float2(0.f, 0.f);
+          if (live1) {
+            e1[j] = a.E[rb1 + o];
+            b1[j] = __ldg(a.B + rb1 + o);
+            x1[j] = a.X[rb1 + o];
+            c1[j] = full1 ? a.C[rb1 + o] : make_float2(0.f, 0.f);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < J; j++) {
+        if (lane + 32 * j < M) {
+          evw[lane + 32 * j] = e0[j];
+          if (live1) evw[M + lane + 32 * j] = e1[j];
+        }
+      }
+      __syncwarp();
+      float racc = 0.f;
+#pragma unroll
+      for (int j = 0; j < J; j++) {
+        if (!use[j]) continue;
+        const int s = sj[j], lft = ax.left[s], rgt = ax.right[s];
+        const long long o = ax.off[s] + qj[j];
+        {
+          const float2* ev = evw;
+          const float2 corr = axis2_corr_sum<TC>(w, t, qj[j], ax.n[s], ev + s * 2 * t,
+                                                 lft >= 0 ? ev + lft * 2 * t + t : nullptr,
+                                                 rgt >= 0 ? ev + rgt * 2 * t : nullptr);
+          a.X[rb0 + o] = layer_step<MODE>(b0[j], e0[j], cadd(c0[j], corr), x0[j], a.alpha, racc);
+        }
+        if (live1) {
+          const float2* ev = evw + M;
+          const float2 corr = axis2_corr_sum<TC>(w, t, qj[j], ax.n[s], ev + s * 2 * t,
+                                                 lft >= 0 ? ev + lft * 2 * t + t : nullptr,
+                                                 rgt >= 0 ? ev + rgt * 2 * t : nullptr);
+          a.X[rb1 + o] = layer_step<MODE>(b1[j], e1[j], cadd(c1[j], corr), x1[j], a.alpha, racc);
+        }
+      }
+      acc += (double)racc;
+      __syncwarp();
+    }
+  }
+  if (a.partials) {
+    const double sum = block_sum(acc, red);
+    finish_block(Finish{a.partials, a.slot0, a.n_total, a.fin, a.hist}, sum, red);
+  }
+}
+
+bool shell_rows_supported(const GridDesc& g) {
+  const int M = (g.ax[2].a > 0 && g.t > 0) ? 2 * g.t * g.ax[2].S : 0;
+  return M <= kShellRowsMaxSlots && g.N0 * g.N1 < (1ll << 31);
+}
+
+cudaError_t launch_shell_rows(const ShellArgs& a, int blocks, cudaStream_t st) {
+  if (!shell_rows_supported(a.g)) return cudaErrorInvalidValue;
+  const int M = (a.g.ax[2].a > 0 && a.g.t > 0) ? 2 * a.g.t * a.g.ax[2].S : 0;
+  const size_t smem = (size_t)8 * 2 * M * sizeof(float2);  // <= 8 KB
+  const bool t8 = a.g.t == 8, one = M <= 32;
+#define MBS_SHELL_ROWS(MODE)                                                                       \
+  if (t8 && one) k_shell_rows<MODE, 8, 1><<<blocks, 256, smem, st>>>(a);                           \
+  else if (t8) k_shell_rows<MODE, 8, 2><<<blocks, 256, smem, st>>>(a);                             \
+  else if (one) k_shell_rows<MODE, 0, 1><<<blocks, 256, smem, st>>>(a);                            \
+  else k_shell_rows<MODE, 0, 2><<<blocks, 256, smem, st>>>(a);
+  if (a.mode == SHELL_UPDATE_ITER) {
+    MBS_SHELL_ROWS(SHELL_UPDATE_ITER)
+  } else if (a.mode == SHELL_UPDATE_RES) {
+    MBS_SHELL_ROWS(SHELL_UPDATE_RES)
+  } else {
+    return cudaErrorInvalidValue;
+  }
+#undef MBS_SHELL_ROWS
+  return cudaGetLastError();
+}
+
 cudaError_t launch_shell(const ShellArgs& a, int blocks, cudaStream_t st) {
   switch (a.mode) {
     case SHELL_UPDATE_ITER: k_shell<SHELL_UPDATE_ITER><<<blocks, 256, 0, st>>>(a); break;

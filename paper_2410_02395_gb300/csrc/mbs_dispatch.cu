@@ -9,13 +9,36 @@ namespace mbs {
 MBS_FFT_GROUP_IDS(MBS_DECLARE_GROUP)
 #undef MBS_DECLARE_GROUP
 
+bool bluestein_group_0(int, int, int, bool, const PassArgs&, int, cudaStream_t, cudaError_t*);
+bool bluestein_group_1(int, int, int, bool, const PassArgs&, int, cudaStream_t, cudaError_t*);
+bool bluestein_group_2(int, int, int, bool, const PassArgs&, int, cudaStream_t, cudaError_t*);
+
 static cudaError_t dispatch(int n, int kind, int axis, bool inv, const PassArgs& a, int nrb, cudaStream_t st) {
   cudaError_t err = cudaErrorInvalidValue;
 #define MBS_TRY_GROUP(k) \
   if (fft_group_##k(n, kind, axis, inv, a, nrb, st, &err)) return err;
   MBS_FFT_GROUP_IDS(MBS_TRY_GROUP)
 #undef MBS_TRY_GROUP
+  if (bluestein_launch(n, kind, axis, inv, a, nrb, st, &err)) return err;
   return cudaErrorInvalidValue;
+}
+
+// Convolution lengths of the Bluestein kernels (compiled FFT lengths).
+static const int kBluesteinM[] = {32, 48, 64, 96, 128, 192, 256, 384, 512};
+
+int bluestein_len(int n) {
+  if (n < 2 || n > 256) return 0;
+  for (int m : kBluesteinM)
+    if (m >= 2 * n - 1) return m;
+  return 0;
+}
+
+bool bluestein_launch(int n, int kind, int axis, bool inv, const PassArgs& a, int nrb, cudaStream_t st,
+                      cudaError_t* err) {
+  const int M = bluestein_len(n);
+  if (!M || !a.bl_chirp || !a.bl_bhat || a.bl_n != n) return false;
+  return bluestein_group_0(M, kind, axis, inv, a, nrb, st, err) || bluestein_group_1(M, kind, axis, inv, a, nrb, st, err) ||
+         bluestein_group_2(M, kind, axis, inv, a, nrb, st, err);
 }
 
 bool fft_size_compiled(int n) {

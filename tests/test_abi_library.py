@@ -57,7 +57,7 @@ def test_workspace_query_and_validation(lib):
         pkg.Plan.workspace_bytes((64, 64, 64), (1, 1, 17))
     assert ei.value.status == 1
     with pytest.raises(pkg.MBSError) as ei:
-        pkg.Plan.workspace_bytes((22, 8, 8), (1, 1, 1))      # 22 = 2 * 11: not a compiled FFT length
+        pkg.Plan.workspace_bytes((262, 8, 8), (1, 1, 1))     # 262 = 2 * 131: above the Bluestein range
     assert ei.value.status == 8
     with pytest.raises(pkg.MBSError) as ei:
         pkg.Plan.workspace_bytes((12, 8, 8), (2, 1, 1), truncation=7)   # t > subdomain edge 6
@@ -73,13 +73,13 @@ def _smooth7(v):
     return v == 1
 
 
-def test_every_7_smooth_edge_up_to_512_is_compiled(lib):
-    """The header's size rule: an edge <= 512 is accepted exactly when its prime
+def test_edge_length_rule(lib):
+    """The header's size rule: every edge up to 256, and edges up to 512 whose prime
     factors are 2, 3, 5 and 7; anything else is MBS_EUNSUPPORTED."""
     import paper_2410_02395_gb300 as pkg
 
     for n in range(1, 520):
-        ok = n <= 512 and _smooth7(n)
+        ok = n <= 256 or (n <= 512 and _smooth7(n))
         try:
             pkg.Plan.workspace_bytes((8, 8, n), (1, 1, 1), truncation=1)
             got = True

@@ -1,7 +1,9 @@
-"""Every compiled FFT length (each n <= 512 with prime factors 2, 3, 5, 7) on each
-axis, so that each length's row, strided and axis-0 pass kernels run once:
-the forward and inverse 3-D DFT of one subdomain (Sec. 3.1) and the
-propagator (L+I)^-1 against the oracle."""
+"""Every mixed-radix FFT length (each n <= 512 with prime factors 2, 3, 5, 7) and
+a spread of Bluestein lengths (other n <= 256) on each axis, so that each
+length's row, strided and axis-0 pass kernels run once: the forward and
+inverse 3-D DFT of one subdomain (Sec. 3.1) and the propagator (L+I)^-1
+against the oracle. Bluestein transforms round a little more (two M-point
+FFTs and the chirp products per transform): 4e-6 there."""
 import numpy as np
 import pytest
 
@@ -23,14 +25,15 @@ def _smooth7(v):
 
 
 LENGTHS = [n for n in range(1, 513) if _smooth7(n)]
+# every Bluestein convolution length M (32 ... 512) and primes across the range
+BLUESTEIN = [11, 13, 17, 22, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61, 67, 97, 101, 127, 131, 167, 191, 211, 251, 254]
 
 
-@pytest.mark.parametrize("axis", [0, 1, 2])
-def test_every_length_on_every_axis(axis):
+def _sweep(axis, lengths, tol):
     import paper_2410_02395_gb300 as pkg
 
     bad = []
-    for n in LENGTHS:
+    for n in lengths:
         shape = [4, 4, 4]
         shape[axis] = n
         shape = tuple(shape)
@@ -44,7 +47,19 @@ def test_every_length_on_every_axis(axis):
         for which, want in (("FFT", fftn3(x)), ("IFFT", ifftn3(x)), ("PROPAGATE", ref.propagate(x))):
             got = plan.apply(which, xd).cpu().numpy().astype(np.complex128)
             err = relative_l2(got, want)
-            if not err < OP_TOL:
+            if not err < tol:
                 bad.append((n, which, err))
         plan.close()
+    return bad
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_every_length_on_every_axis(axis):
+    bad = _sweep(axis, LENGTHS, OP_TOL)
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_bluestein_lengths_on_every_axis(axis):
+    bad = _sweep(axis, BLUESTEIN, 4e-6)
     assert not bad, bad

@@ -55,11 +55,18 @@ CASES = {
     "t_sweep_6": dict(shape=(64, 48, 40), split=(2, 2, 2), t=6),
     "t_sweep_12": dict(shape=(64, 48, 40), split=(2, 2, 2), t=12),
     "t_sweep_16": dict(shape=(64, 48, 40), split=(2, 2, 2), t=16),
+    # t = 8 (the width of the benchmark workloads) takes the kernels specialised for it
+    "t8_2x2x2": dict(shape=(40, 36, 48), split=(2, 2, 2), t=8),
+    "t8_3x1x3": dict(shape=(48, 20, 60), split=(3, 1, 3), t=8, periodic=(False, True, False)),
+    # edges with prime factors above 7 (Bluestein transforms) on every axis
+    "prime_sizes": dict(shape=(84, 47, 53), split=(2, 1, 1), t=4, split_sizes=[[41, 43], [47], [53]]),
+    "prime_mixed": dict(shape=(40, 22, 59), split=(2, 2, 1), t=3, split_sizes=[[16, 24], [11, 11], [59]],
+                        periodic=(False, False, True)),
 }
 
 
-TF32_CASES = ["cube_2x2x2", "uneven_sizes", "single_nonperiodic", "periodic_split_seam", "t_sweep_6"]
-RES_CASES = ["cube_2x2x2", "single_periodic", "ragged_3x1x2", "line_1d"]
+TF32_CASES = ["cube_2x2x2", "uneven_sizes", "single_nonperiodic", "periodic_split_seam", "t_sweep_6", "prime_sizes"]
+RES_CASES = ["cube_2x2x2", "single_periodic", "ragged_3x1x2", "line_1d", "t8_2x2x2", "t_sweep_16", "prime_sizes"]
 
 
 @pytest.fixture(scope="module", params=sorted(CASES) + ["tf32:" + c for c in TF32_CASES] +
