@@ -62,8 +62,10 @@ def kernel_bytes_per_voxel(kind, fr):
         "mid_axis0": 2 * f,
         "strided_inv": 2 * f,
         "rows_last": 4 * f,                    # FFT buffer, x, B in; x (or e on the layers) out
-        "corr_e": 2 * fr["L"] * f,             # layers of e in, E e out on them
-        "shell_update": 5 * fr["sh"] * f,      # e, E e, x, B in and x out on the layer voxels
+        # axis-0/1 layers of e in, E e out on them (axis 2 is computed inside the layer update)
+        "corr_e": 2 * fr["L01"] * f,
+        # e, x, B in and x out on the layer voxels; E_0 e + E_1 e in on the axis-0/1 layer rows
+        "shell_update": 4 * fr["sh"] * f + fr["g01"] * f,
     }[kind]
 
 
@@ -76,8 +78,9 @@ def layer_fractions(info):
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel from one ncu capture of the current kernels (see profiles/).
-MEASURED_TRAFFIC = {("C2", "rows_first"): 419167232}
+# dominant kernel from one ncu capture of the current kernels (see profiles/);
+# empty until the current kernels have been captured.
+MEASURED_TRAFFIC = {}
 
 
 def read_peaks():
@@ -309,6 +312,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_TEXT),
                     help="benchmark workload (default: the C2 configuration)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 3xTF32-correction timing")
+    ap.add_argument("--t-sweep", default="", help="comma-separated truncation widths: ms per iteration for each "
+                    "on the same workload (Sec. 4.2.1, Fig. 7c)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -445,6 +450,24 @@ def main():
                         "seconds": time.perf_counter() - t0, "form": "residual form, FP32 corrections"}
             pr.close()
 
+        # ---- truncation sweep: iteration time against t ------------------------
+        tsweep = None
+        if args.t_sweep:
+            tsweep = []
+            for tv in [int(v) for v in args.t_sweep.split(",") if v]:
+                kt = dict(kw, truncation=tv)
+                pt = pkg.Plan(shape, params["pixel"], params["wavelength"], n_dev, **kt)
+                pt.set_source(src_dev)
+                Kt = max(10, K // 4)
+                pt.iterate(max(args.warmup, 3), 0.0, no_poll=True)
+                torch.cuda.synchronize(dev)
+                ev0.record(stream)
+                pt.iterate(Kt, 0.0, no_poll=True)
+                ev1.record(stream)
+                torch.cuda.synchronize(dev)
+                tsweep.append({"t": tv, "ms_per_step": ev0.elapsed_time(ev1) / Kt, "c_abs": abs(pt.info()["c"])})
+                pt.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         os.environ.setdefault("OMP_NUM_THREADS", "1")
@@ -472,6 +495,8 @@ def main():
             "mixed": mixed,
             "time_to_tol": ttt_line,
         }
+        if args.t_sweep:
+            line["t_sweep"] = tsweep
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -1,0 +1,43 @@
+"""Truncation sweep on the GPU (Sec. 4.2.1): every compiled truncation width t
+on one geometry with 32-voxel subdomains, against the oracle's truncated
+operator, and the distance to the undecomposed operator falling as t grows
+(Fig. 7a: the error with respect to a one-domain simulation decays with t)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import Problem, relative_l2  # noqa: E402
+from synth import random_field  # noqa: E402
+from tests import dense_reference as dr  # noqa: E402
+
+T_VALUES = list(range(1, 17)) + [20, 24, 32]
+SHAPE = (64, 4, 4)
+KW = dict(boundary_widths=((4, 4), (0, 0), (0, 0)), split=(2, 1, 1), periodic=(False, True, True))
+
+
+def test_every_truncation_width():
+    import paper_2410_02395_gb300 as pkg
+
+    rng = np.random.default_rng(8)
+    n = (1.0 + 0.3 * rng.random(SHAPE)).astype(np.complex64)
+    x = random_field(SHAPE, seed=9).astype(np.complex128)
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    bad, to_global = [], []
+    for t in T_VALUES:
+        plan = pkg.Plan(SHAPE, 0.25, 1.0, torch.from_numpy(n).cuda(), truncation=t, **KW)
+        ref = Problem(n, 0.25, 1.0, widths=KW["boundary_widths"], split=KW["split"], periodic=KW["periodic"], t=t)
+        got = plan.apply("A", xd).cpu().numpy().astype(np.complex128)
+        plan.close()
+        err = relative_l2(got, ref.apply_A(x))
+        if not err < 2e-6:
+            bad.append((t, err))
+        Ag = dr.dense_A_global(SHAPE, ref.h, ref.periodic, ref.k2, ref.c)
+        to_global.append(relative_l2(got, (Ag @ x.ravel()).reshape(SHAPE)))
+    assert not bad, bad
+    # distance to the undecomposed operator: falls with t, roughly like 1/t
+    assert to_global[T_VALUES.index(32)] < 0.1 * to_global[T_VALUES.index(2)]
+    for lo, hi in ((2, 4), (4, 8), (8, 16), (16, 32)):
+        assert to_global[T_VALUES.index(hi)] < to_global[T_VALUES.index(lo)]
