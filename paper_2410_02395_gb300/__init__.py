@@ -152,7 +152,7 @@ class Plan:
     def __init__(self, shape, pixel_size, wavelength, refractive_index, boundary_widths=((0, 0),) * 3,
                  split=(1, 1, 1), truncation=8, alpha=0.75, periodic=(False, False, False), kappa=0.5,
                  split_sizes=None, graph_iters=0, no_graph=False, corr_tf32=False, residual_form=False,
-                 stream=None, workspace=None):
+                 no_tma=False, stream=None, workspace=None):
         self.lib = load_library()
         self.shape = tuple(int(s) for s in shape)
         opts = _Options()
@@ -162,7 +162,8 @@ class Plan:
         opts.periodic_mask = sum((1 << d) for d in range(3) if periodic[d])
         opts.absorb_kappa = float(kappa)
         opts.graph_iters = int(graph_iters)
-        opts.flags = (1 if no_graph else 0) | (2 if corr_tf32 else 0) | (4 if residual_form else 0)
+        opts.flags = (1 if no_graph else 0) | (2 if corr_tf32 else 0) | (4 if residual_form else 0) | \
+            (8 if no_tma else 0)
         self._split_sizes = None
         if split_sizes is not None:
             flat = [int(v) for d in range(3) for v in split_sizes[d]]

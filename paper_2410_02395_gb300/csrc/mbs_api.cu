@@ -139,6 +139,8 @@ struct mbs_plan {
   // Bluestein edges (a prime factor above 7): chirp (n) and spectra (2M) per edge
   std::map<int, float2*> bl_chirp, bl_bhat;
   bool bl_axis2;  // an axis-2 edge is a Bluestein length (no fused axis-2 corrections then)
+  // tensor maps of the TMA-fed passes, keyed by axis * 65536 + edge
+  std::map<int, CUtensorMap> tmaps;
   double* partials;
   int n_rows_partials, n_shell_partials;
   DevState* state;
@@ -633,6 +635,20 @@ cudaError_t run_corr(mbs_plan* p, const float2* F, float2* C, const DevState* st
   return run_corr_rec(p, F, C, state, nullptr, 0, axis2);
 }
 
+// Axis-1 pass and axis-0 pass of one edge group: TMA-fed where the plan has a
+// tensor map for it, register-fed otherwise.
+cudaError_t strided_pass(const mbs_plan* p, const PassArgs& a, int n, bool inv) {
+  auto it = p->tmaps.find(1 * 65536 + n);
+  if (it != p->tmaps.end()) return launch_strided_tma(n, 1, inv, a, it->second, p->stream);
+  return launch_strided(n, 1, inv, a, p->stream);
+}
+cudaError_t mid_pass(const mbs_plan* p, const PassArgs& a, int n) {
+  auto it = p->tmaps.find(0 * 65536 + n);
+  if (it != p->tmaps.end() && (a.mode == MID_PROP || a.mode == MID_LSYM))
+    return launch_mid_tma(n, a, it->second, p->stream);
+  return launch_mid(n, a, p->stream);
+}
+
 // The forward half shared by the iteration and several operators:
 // rows_first (mode), strided axis-1 forward, mid (mode), strided axis-1 inverse.
 cudaError_t run_transform_chain(mbs_plan* p, PassArgs a, int first_mode, int mid_mode, Recorder* rec) {
@@ -654,7 +670,7 @@ cudaError_t run_transform_chain(mbs_plan* p, PassArgs a, int first_mode, int mid
     memcpy(a.subs, gy.subs, sizeof(a.subs));
     set_len_tables(p, a, gy.n);
     if (rec) rec->begin(KK_STRIDED_FWD);
-    e = launch_strided(gy.n, 1, false, a, p->stream);
+    e = strided_pass(p, a, gy.n, false);
     if (rec) rec->end();
     if (e) return e;
   }
@@ -664,7 +680,7 @@ cudaError_t run_transform_chain(mbs_plan* p, PassArgs a, int first_mode, int mid
     memcpy(a.subs, gx.subs, sizeof(a.subs));
     set_len_tables(p, a, gx.n);
     if (rec) rec->begin(KK_MID);
-    e = launch_mid(gx.n, a, p->stream);
+    e = mid_pass(p, a, gx.n);
     if (rec) rec->end();
     if (e) return e;
   }
@@ -675,7 +691,7 @@ cudaError_t run_transform_chain(mbs_plan* p, PassArgs a, int first_mode, int mid
     memcpy(a.subs, gy.subs, sizeof(a.subs));
     set_len_tables(p, a, gy.n);
     if (rec) rec->begin(KK_STRIDED_INV);
-    e = launch_strided(gy.n, 1, true, a, p->stream);
+    e = strided_pass(p, a, gy.n, true);
     if (rec) rec->end();
     if (e) return e;
   }
@@ -928,6 +944,13 @@ mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double p
     return cleanup(fail(MBS_ECUDA, "pinned allocation failed"));
   st = upload_tables(p);
   if (st) return cleanup(st);
+  if (!(p->flags & MBS_FLAG_NO_TMA)) {
+    for (int d = 0; d < 2; d++)
+      for (auto& gsz : p->groups[d]) {
+        CUtensorMap tm;
+        if (gsz.n > 1 && make_tma_map(&tm, p->K, p->g, d, gsz.n)) p->tmaps[d * 65536 + gsz.n] = tm;
+      }
+  }
   // refractive index: use the device array directly, or stage it through src
   const float2* n_dev = nullptr;
   if (is_device_ptr(refractive_index)) {

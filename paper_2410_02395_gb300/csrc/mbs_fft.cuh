@@ -262,8 +262,9 @@ template <int N> struct PlanOf<N, true> { static constexpr RadixPlan value = rev
 // Stage driver: stage S of the plan with NS = product of the previous radices.
 // FIRST_SMEM / LAST_SMEM say whether the first stage's loader and the last
 // stage's storer touch the shared tile (then the stage needs its mid barrier).
-template <int N, int W, bool INV, bool REV, int S, int NS, bool FIRST_SMEM, bool LAST_SMEM, class Ld, class St>
-__device__ __forceinline__ void fft_run(int warp, int lane, float2 (*sm)[kPad], const float2* __restrict__ tw,
+template <int N, int W, bool INV, bool REV, int S, int NS, bool FIRST_SMEM, bool LAST_SMEM, int PITCH, class Ld,
+          class St>
+__device__ __forceinline__ void fft_run(int warp, int lane, float2 (*sm)[PITCH], const float2* __restrict__ tw,
                                         Ld first_ld, St last_st) {
   constexpr RadixPlan P = PlanOf<N, REV>::value;
   constexpr int R = P.r[S];
@@ -286,8 +287,8 @@ __device__ __forceinline__ void fft_run(int warp, int lane, float2 (*sm)[kPad], 
 
 // Forward stages S..nr-2 of plan(N) (all but the last), leaving the tile in
 // shared memory. Used before the turn of fft_fwd_mul_inv.
-template <int N, int W, int S, int NS, bool FIRST_SMEM, class Ld>
-__device__ __forceinline__ void fft_run_partial(int warp, int lane, float2 (*sm)[kPad], const float2* __restrict__ tw,
+template <int N, int W, int S, int NS, bool FIRST_SMEM, int PITCH, class Ld>
+__device__ __forceinline__ void fft_run_partial(int warp, int lane, float2 (*sm)[PITCH], const float2* __restrict__ tw,
                                                 Ld first_ld) {
   constexpr RadixPlan P = make_plan(N);
   constexpr int R = P.r[S];
@@ -342,8 +343,8 @@ __device__ __forceinline__ void turn_stage(int warp, const float2* __restrict__ 
 
 // Forward stages 0..nr-2 of plan(N), the turn, then inverse stages 1..nr-1 of
 // the reversed plan. Loader/storer semantics as in fft_run.
-template <int N, int W, bool FIRST_SMEM, bool LAST_SMEM, class Ld, class St, class Mul>
-__device__ __forceinline__ void fft_fwd_mul_inv(int warp, int lane, float2 (*sm)[kPad], const float2* __restrict__ tw,
+template <int N, int W, bool FIRST_SMEM, bool LAST_SMEM, int PITCH, class Ld, class St, class Mul>
+__device__ __forceinline__ void fft_fwd_mul_inv(int warp, int lane, float2 (*sm)[PITCH], const float2* __restrict__ tw,
                                                 Ld first_ld, St last_st, Mul mul) {
   constexpr RadixPlan P = make_plan(N);
   constexpr int RL = P.r[P.nr - 1];

@@ -543,8 +543,10 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_mid_pl
 inline size_t tile_bytes(int n) { return (size_t)n * kPad * sizeof(float2); }
 
 // Resident CTAs per SM asked of the register allocator for the axis-0 pass
-// (forward + multiplier + inverse keeps more values live than a single pass).
-constexpr int mid_min_blocks(int n) { return 24 / warps_for(n) > 1 ? 24 / warps_for(n) : 1; }
+// (forward + multiplier + inverse): as many as the other passes. At n = 128 this
+// spills a few registers but runs 4 % faster than 3 CTAs per SM without spills
+// (measured on the 256^3 workload).
+constexpr int mid_min_blocks(int n) { return 32 / warps_for(n) > 1 ? 32 / warps_for(n) : 1; }
 
 // Per kernel (keyed by its address): above 48 KB, the dynamic shared-memory
 // opt-in for the largest size requested so far. The L1/shared split is left to

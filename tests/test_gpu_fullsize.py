@@ -116,3 +116,19 @@ def test_c2_residual_monotone_from_one(c2):
     h = plan.history(300)
     assert len(h) == 300 and h[0] == 1.0
     assert np.all(h[1:] <= h[:-1] * (1 + 1e-5))
+
+
+def test_c2_tma_passes_equal_register_fed_passes(c2):
+    """The TMA-fed axis-1/axis-0 passes run the same arithmetic as the register-fed
+    ones: iterates agree bit for bit."""
+    params, n, src, plan = c2
+    K = 2 * plan.info()["graph_iters"]
+    plan.set_source(torch.from_numpy(src).cuda())
+    plan.iterate(K, 0.0, no_poll=True)
+    xt = plan.field(like=torch.zeros(1, device="cuda"))
+    other = _plan(params, n, no_tma=True)
+    other.set_source(torch.from_numpy(src).cuda())
+    other.iterate(K, 0.0, no_poll=True)
+    xr = other.field(like=torch.zeros(1, device="cuda"))
+    other.close()
+    assert torch.equal(xt, xr)
