@@ -89,10 +89,10 @@ typedef enum mbs_operator {
                                         arithmetic; in complex64 the residual has no floor set by ||x||,
                                         so tolerances below that floor are reachable. Costs about
                                         24 B per voxel and iteration more (x and its low word).      */
-#define MBS_FLAG_NO_TMA (1u << 3) /* feed the axis-1 and axis-0 passes with per-thread global loads
-                                     instead of tensor-map (TMA) copies into double-buffered shared
-                                     memory. Default: TMA where the edge has TMA kernels (32, 64,
-                                     128, 256) and the grid's row pitch is a multiple of 16 bytes. */
+#define MBS_FLAG_NO_TMA (1u << 3) /* feed the axis-1 FFT passes with per-thread global loads instead
+                                     of tensor-map (TMA) copies into double-buffered shared memory.
+                                     Default: TMA where the edge has TMA kernels (32, 64, 128, 256)
+                                     and the grid's row pitch is a multiple of 16 bytes.          */
 
 typedef struct mbs_options {
   int32_t truncation;        /* t, the kept edge width (Sec. 3, Fig. 5); 0 -> 8 (Sec. 3.3)      */

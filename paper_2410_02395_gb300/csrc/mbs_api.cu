@@ -635,18 +635,15 @@ cudaError_t run_corr(mbs_plan* p, const float2* F, float2* C, const DevState* st
   return run_corr_rec(p, F, C, state, nullptr, 0, axis2);
 }
 
-// Axis-1 pass and axis-0 pass of one edge group: TMA-fed where the plan has a
-// tensor map for it, register-fed otherwise.
+// Axis-1 pass of one edge group: TMA-fed where the plan has a tensor map for
+// it, register-fed otherwise. (A TMA-fed axis-0 pass, forward transform,
+// propagator and inverse per tile, measured slower than the register-fed one at
+// four CTAs per SM, 78.9 against 76.1 us on the 256^3 workload: it is
+// issue-bound, not waiting on memory.)
 cudaError_t strided_pass(const mbs_plan* p, const PassArgs& a, int n, bool inv) {
   auto it = p->tmaps.find(1 * 65536 + n);
   if (it != p->tmaps.end()) return launch_strided_tma(n, 1, inv, a, it->second, p->stream);
   return launch_strided(n, 1, inv, a, p->stream);
-}
-cudaError_t mid_pass(const mbs_plan* p, const PassArgs& a, int n) {
-  auto it = p->tmaps.find(0 * 65536 + n);
-  if (it != p->tmaps.end() && (a.mode == MID_PROP || a.mode == MID_LSYM))
-    return launch_mid_tma(n, a, it->second, p->stream);
-  return launch_mid(n, a, p->stream);
 }
 
 // The forward half shared by the iteration and several operators:
@@ -680,7 +677,7 @@ cudaError_t run_transform_chain(mbs_plan* p, PassArgs a, int first_mode, int mid
     memcpy(a.subs, gx.subs, sizeof(a.subs));
     set_len_tables(p, a, gx.n);
     if (rec) rec->begin(KK_MID);
-    e = mid_pass(p, a, gx.n);
+    e = launch_mid(gx.n, a, p->stream);
     if (rec) rec->end();
     if (e) return e;
   }
@@ -945,11 +942,10 @@ mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double p
   st = upload_tables(p);
   if (st) return cleanup(st);
   if (!(p->flags & MBS_FLAG_NO_TMA)) {
-    for (int d = 0; d < 2; d++)
-      for (auto& gsz : p->groups[d]) {
-        CUtensorMap tm;
-        if (gsz.n > 1 && make_tma_map(&tm, p->K, p->g, d, gsz.n)) p->tmaps[d * 65536 + gsz.n] = tm;
-      }
+    for (auto& gsz : p->groups[1]) {
+      CUtensorMap tm;
+      if (gsz.n > 1 && make_tma_map(&tm, p->K, p->g, 1, gsz.n)) p->tmaps[1 * 65536 + gsz.n] = tm;
+    }
   }
   // refractive index: use the device array directly, or stage it through src
   const float2* n_dev = nullptr;
@@ -1178,6 +1174,7 @@ mbs_status mbs_iterate(mbs_plan* p, int32_t n_iter, double tol, int32_t no_poll,
   if (residual) *residual = hs.eps;
   if (hs.status == MBS_ENAN) return fail(MBS_ENAN, "residual is not finite");
   if (hs.status == MBS_EDIVERGE) return fail(MBS_EDIVERGE, "residual kept rising");
+  if (hs.status == MBS_ETIMEOUT) return fail(MBS_ETIMEOUT, "a bounded wait for a tensor-map copy expired");
   if (hs.iter > 0 && hs.eps < tol) return MBS_OK;
   return MBS_ENOCONV;
 }

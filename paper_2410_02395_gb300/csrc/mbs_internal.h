@@ -140,13 +140,12 @@ cudaError_t launch_rows_first(int n, const PassArgs& a, int nrows_blocks, cudaSt
 cudaError_t launch_rows_last(int n, const PassArgs& a, int nrows_blocks, cudaStream_t st);
 cudaError_t launch_strided(int n, int axis, bool inv, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_mid(int n, const PassArgs& a, cudaStream_t st);
-// TMA-fed axis-1 / axis-0 passes (mbs_tma.cu): whether edge n has them, the
-// tensor map over the FFT buffer K for a pass along `axis` (false: no map, use
-// the register-fed kernels), and the launchers.
+// TMA-fed strided passes (mbs_tma.cu): whether edge n has them, the tensor map
+// over the FFT buffer K for a pass along `axis` (false: no map, use the
+// register-fed kernels), and the launcher.
 bool tma_len_supported(int n);
 bool make_tma_map(CUtensorMap* tm, void* K, const GridDesc& g, int axis, int n);
 cudaError_t launch_strided_tma(int n, int axis, bool inv, const PassArgs& a, const CUtensorMap& tm, cudaStream_t st);
-cudaError_t launch_mid_tma(int n, const PassArgs& a, const CUtensorMap& tm, cudaStream_t st);
 // Bluestein FFT lengths: the M of the convolution for edge n (0: n has no
 // compiled Bluestein form), and the launcher the dispatch falls back to.
 int bluestein_len(int n);

@@ -17,6 +17,7 @@
 // distinct subdomain size along d; grid.z (or .y) selects the subdomain.
 #pragma once
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 
 #include <cuda_bf16.h>
@@ -200,36 +201,48 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
       wsm[m] = a.cW[aa * t + bb].y;
     }
   }
-  for (int k0 = 0; k0 < PERT; k0 += CH) {
-    float2 xv[CH], bv[CH], cv[CH];
+  // Tiles with all 32 rows inside the grid and none in the source box (almost
+  // all) take a loop without those per-voxel tests.
+  auto load = [&](auto full_tile) {
+    constexpr bool FULL = decltype(full_tile)::value;
+    for (int k0 = 0; k0 < PERT; k0 += CH) {
+      float2 xv[CH], bv[CH], cv[CH];
 #pragma unroll
-    for (int c = 0; c < CH; c++) {
-      int r, e;
-      const bool ok = TileMap<N, NT>::at(tid, k0 + c, r, e);
-      xv[c] = bv[c] = cv[c] = make_float2(0.f, 0.f);
-      if (ok && rt.ok(r)) {
-        const unsigned o = (unsigned)r * n2 + (unsigned)e;
-        xv[c] = __ldg(Xt + o);
-        if (iter) {
-          bv[c] = __ldg(Bt + o);
-          if (rt.lay(r) || (!a.fuse_e2 && in_layer2<N>(a, e))) cv[c] = Kt[o];  // E x from the correction kernels
+      for (int c = 0; c < CH; c++) {
+        int r, e;
+        const bool ok = TileMap<N, NT>::at(tid, k0 + c, r, e);
+        xv[c] = bv[c] = cv[c] = make_float2(0.f, 0.f);
+        if (ok && (FULL || rt.ok(r))) {
+          const unsigned o = (unsigned)r * n2 + (unsigned)e;
+          xv[c] = __ldg(Xt + o);
+          if (iter) {
+            bv[c] = __ldg(Bt + o);
+            if (rt.lay(r) || (!a.fuse_e2 && in_layer2<N>(a, e))) cv[c] = Kt[o];  // E x from the correction kernels
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CH; c++) {
+        int r, e;
+        if (TileMap<N, NT>::at(tid, k0 + c, r, e)) {
+          float2 u = xv[c];
+          if (iter && (FULL || rt.ok(r))) {
+            u = csub(cmul(bv[c], xv[c]), cv[c]);
+            if (!FULL) {
+              const long long i2 = off2 + e;
+              if (rt.in_src(r) && i2 >= a.sbox[4] && i2 < a.sbox[5]) u = cadd(u, cmul(a.mc, a.S[rt.base(r) + e]));
+            }
+          }
+          sm[e][r] = u;
         }
       }
     }
-#pragma unroll
-    for (int c = 0; c < CH; c++) {
-      int r, e;
-      if (TileMap<N, NT>::at(tid, k0 + c, r, e)) {
-        float2 u = xv[c];
-        if (iter && rt.ok(r)) {
-          u = csub(cmul(bv[c], xv[c]), cv[c]);
-          const long long i2 = off2 + e;
-          if (rt.in_src(r) && i2 >= a.sbox[4] && i2 < a.sbox[5]) u = cadd(u, cmul(a.mc, a.S[rt.base(r) + e]));
-        }
-        sm[e][r] = u;
-      }
-    }
-  }
+  };
+  const bool full_tile = rt.valid == 0xffffffffu && rt.src == 0u;
+  if (full_tile)
+    load(std::true_type{});
+  else
+    load(std::false_type{});
   if (e2) {
     // Warp w corrects tile elements q(k) for k = w, w + W, ... < 2t, lane = row:
     //   first t: u -= sum_b cW[b][q]  (x_left[n_l-t+b] - x[n-t+b])

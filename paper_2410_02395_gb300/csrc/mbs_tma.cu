@@ -1,5 +1,5 @@
-// TMA-fed axis-1 and axis-0 passes (mbs_tma.cuh): instantiations, tensor maps
-// and launchers.
+// TMA-fed strided passes (mbs_tma.cuh): instantiations, tensor maps and
+// launchers.
 #include <mutex>
 #include <unordered_map>
 
@@ -84,7 +84,7 @@ static cudaError_t run_tma(int kind, int axis, bool inv, const PassArgs& a, cons
   const size_t smem = (size_t)2 * N * 32 * sizeof(float2);
   const int threads = 32 * warps_for(N);
   const int gx = (int)((a.g.N2 + 31) / 32);
-  const int ny = (int)(kind == 3 || axis == 0 ? a.g.N1 : a.g.N0);
+  const int ny = (int)(axis == 0 ? a.g.N1 : a.g.N0);
   const int ntiles = gx * ny * a.nsub;
   if (ntiles == 0) return cudaSuccess;
   cudaError_t e;
@@ -92,20 +92,11 @@ static cudaError_t run_tma(int kind, int axis, bool inv, const PassArgs& a, cons
   e = set_smem(KER, smem);                                       \
   if (e) return e;                                               \
   KER<<<persistent_blocks(KER, threads, smem, ntiles), threads, smem, st>>>(a, tm);
-  if (kind == 3) {
-    MBS_TMA_LAUNCH(k_mid_tma<N>)
-  } else if (axis == 1) {
-    if (inv) {
-      MBS_TMA_LAUNCH((k_strided_tma<N, 1, true>))
-    } else {
-      MBS_TMA_LAUNCH((k_strided_tma<N, 1, false>))
-    }
+  if (axis != 1) return cudaErrorInvalidValue;  // the axis-0 pass is register-fed (see strided_pass)
+  if (inv) {
+    MBS_TMA_LAUNCH((k_strided_tma<N, 1, true>))
   } else {
-    if (inv) {
-      MBS_TMA_LAUNCH((k_strided_tma<N, 0, true>))
-    } else {
-      MBS_TMA_LAUNCH((k_strided_tma<N, 0, false>))
-    }
+    MBS_TMA_LAUNCH((k_strided_tma<N, 1, false>))
   }
 #undef MBS_TMA_LAUNCH
   return cudaGetLastError();
@@ -116,19 +107,6 @@ cudaError_t launch_strided_tma(int n, int axis, bool inv, const PassArgs& a, con
 #define MBS_TMA_CASE(n) \
   case n:               \
     return run_tma<n>(2, axis, inv, a, tm, st);
-    MBS_TMA_SIZES(MBS_TMA_CASE)
-#undef MBS_TMA_CASE
-    default:
-      return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t launch_mid_tma(int n, const PassArgs& a, const CUtensorMap& tm, cudaStream_t st) {
-  if (a.mode != MID_PROP && a.mode != MID_LSYM) return cudaErrorInvalidValue;
-  switch (n) {
-#define MBS_TMA_CASE(n) \
-  case n:               \
-    return run_tma<n>(3, 0, false, a, tm, st);
     MBS_TMA_SIZES(MBS_TMA_CASE)
 #undef MBS_TMA_CASE
     default:

@@ -1,4 +1,4 @@
-// Axis-1 and axis-0 passes fed by the Tensor Memory Accelerator.
+// Strided (axis-1) FFT passes fed by the Tensor Memory Accelerator.
 //
 // A tile is 32 consecutive axis-2 positions x one subdomain's n positions
 // along the pass axis (one i0, or one i1). It is a box of the 3-D tensor map
@@ -156,48 +156,6 @@ __global__ void __launch_bounds__(32 * warps_for(N), tma_min_blocks(N)) k_stride
       if (valid) K[base + e * stride] = v;
     };
     fft_run<N, W, INV, false, 0, 1, true, false>(warp, lane, sm, a.tw, sld, gst);
-  });
-}
-
-// Axis-0 pass (MID_PROP / MID_LSYM): forward transform, multiplier, inverse.
-template <int N>
-__global__ void __launch_bounds__(32 * warps_for(N), tma_min_blocks(N)) k_mid_tma(const __grid_constant__ PassArgs a,
-                                                                  const __grid_constant__ CUtensorMap tm) {
-  constexpr int W = warps_for(N);
-  extern __shared__ __align__(1024) float2 dyn[];
-  __shared__ __align__(8) uint64_t bar[2];
-  if (a.state && a.state->done) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float2 c = a.c, ck0 = a.ck0;
-  const bool prop = a.mode == MID_PROP;
-  float2* K = a.K;
-  tma_tiles<N, 0>(a, &tm, dyn, bar, [&](float2 (*sm)[32], const TmaTile& tl) {
-    const int j = a.subs[tl.js];
-    const int off0 = a.g.ax[0].off[j];
-    const long long i1 = tl.y;
-    const long long i2 = (long long)tl.ib * 32 + lane;
-    const bool valid = i2 < a.g.N2;
-    const long long i2c = valid ? i2 : 0;
-    const long long base = (long long)off0 * a.g.N1 * a.g.N2 + i1 * a.g.N2 + i2;
-    const long long stride = a.g.N1 * a.g.N2;
-    const float pl = a.tb.p2[1][i1] + a.tb.p2[2][i2c];
-    const float sc = a.tb.invn[0][off0] * a.tb.invn[1][i1] * a.tb.invn[2][i2c];
-    const float* p20 = a.tb.p2[0] + off0;
-    auto sld = [&](int e) { return sm[e][lane]; };
-    auto gst = [&](int e, float2 v) {
-      if (valid) K[base + e * stride] = v;
-    };
-    auto mul = [&](int e, float2 v) {
-      const float p2 = __ldg(p20 + e) + pl;
-      const float dx = fmaf(-c.x, p2, ck0.x), dy = fmaf(-c.y, p2, ck0.y);  // c (k0^2 - |p|^2)
-      if (prop) {
-        const float ex = dx + 1.f;
-        const float inv = sc * __frcp_rn(fmaf(ex, ex, dy * dy));
-        return cmul(v, make_float2(ex * inv, -dy * inv));
-      }
-      return cmul(v, make_float2(dx * sc, dy * sc));
-    };
-    fft_fwd_mul_inv<N, W, true, false>(warp, lane, sm, a.tw, sld, gst, mul);
   });
 }
 
