@@ -214,12 +214,13 @@ __global__ void __launch_bounds__(32 * warps_for(M), fft_min_blocks(M)) k_mid_bl
   }
   if (mode == MID_PROP || mode == MID_LSYM) {
     const float2 c = a.c, ck0 = a.ck0;
+    // c is purely imaginary (Eq. c_scale2), so Re c(k0^2 - |p|^2) = Re(c k0^2) for every p
+    const float dx = ck0.x, ex = dx + 1.f;
     for (int k = warp; k < n; k += W) {
       const float p2 = __ldg(m.p20 + k) + m.pl;
-      const float dx = fmaf(-c.x, p2, ck0.x), dy = fmaf(-c.y, p2, ck0.y);  // c (k0^2 - |p|^2)
+      const float dy = fmaf(-c.y, p2, ck0.y);  // Im c(k0^2 - |p|^2)
       float2 mul;
       if (mode == MID_PROP) {
-        const float ex = dx + 1.f;
         const float inv = m.sc * __frcp_rn(fmaf(ex, ex, dy * dy));
         mul = make_float2(ex * inv, -dy * inv);
       } else {

@@ -507,11 +507,12 @@ __global__ void __launch_bounds__(32 * warps_for(N), MIN_BLOCKS) k_mid_turn(cons
     if (m.valid) K[m.base + e * m.stride] = v;
   };
   const bool prop = a.mode == MID_PROP;
+  // c is purely imaginary (Eq. c_scale2), so Re c(k0^2 - |p|^2) = Re(c k0^2) for every p
+  const float dx = ck0.x, ex = dx + 1.f;
   auto mul = [&](int e, float2 v) {
     const float p2 = __ldg(m.p20 + e) + m.pl;
-    const float dx = fmaf(-c.x, p2, ck0.x), dy = fmaf(-c.y, p2, ck0.y);  // c (k0^2 - |p|^2)
+    const float dy = fmaf(-c.y, p2, ck0.y);  // Im c(k0^2 - |p|^2)
     if (prop) {
-      const float ex = dx + 1.f;
       const float inv = m.sc * __frcp_rn(fmaf(ex, ex, dy * dy));
       return cmul(v, make_float2(ex * inv, -dy * inv));
     }
