@@ -45,6 +45,8 @@ WORKLOAD_TEXT = {
           "(grids 80^3-120^3), each split 2x2x2 into 7-smooth halves, t=8, same spheres, point sources; "
           "one CUDA graph over all solves",
     "C5": "C5: 1280^3 grid at lambda/4, 4x4x4 subdomains of 320^3, t=8, spheres to 30% fill, point source",
+    "C2P": "C2P: the C2 recipe on a 246^3 grid, 2x2x2 subdomains of 123^3 (123 = 3 x 41: Bluestein transforms "
+           "on every axis), t=8",
 }
 METRIC = "voxel-iterations/s on 1 GB300 (mixed vs plain FP32, ≤1e-4 vs FP64); time-to-tol"
 UNIT = "voxel-iterations/s"
@@ -53,11 +55,15 @@ UNIT = "voxel-iterations/s"
 # launches in one iteration; complex64 = 8 B). fr holds layer fractions:
 #   L   = sum over corrected axes of 2t*S_d/N_d,  L01 the same over axes 0 and 1,
 #   sh  = fraction of voxels in any boundary layer, g01 = in an axis-0/1 layer.
+#   When an axis-2 edge has a prime factor above 7 (Bluestein transforms) the
+#   first pass does not compute E_2 x: the correction launches on x then cover
+#   axis 2 too, and the first pass reads E x on every boundary-layer voxel.
 def kernel_bytes_per_voxel(kind, fr):
     f = 8.0
+    x_layers, first_layers = (fr["L01"], fr["g01"]) if fr["fused2"] else (fr["L"], fr["sh"])
     return {
-        "corr_x": 2 * fr["L01"] * f,           # axis-0/1 layers of x in, E x out on them
-        "rows_first": 3 * f + fr["g01"] * f,   # x, B in, FFT buffer out, E_0 x + E_1 x in on those rows
+        "corr_x": 2 * x_layers * f,            # layers of x in, E x out on them
+        "rows_first": 3 * f + first_layers * f,  # x, B in, FFT buffer out, E x in on the layer voxels it needs
         "strided_fwd": 2 * f,
         "mid_axis0": 2 * f,
         "strided_inv": 2 * f,
@@ -74,7 +80,15 @@ def layer_fractions(info):
     fd = [min(1.0, 2.0 * t * len(s) / sum(s)) if info["a"][d] > 0 else 0.0 for d, s in enumerate(info["sizes"])]
     sh = 1.0 - (1.0 - fd[0]) * (1.0 - fd[1]) * (1.0 - fd[2])
     g01 = 1.0 - (1.0 - fd[0]) * (1.0 - fd[1])
-    return {"L": sum(fd), "L01": fd[0] + fd[1], "sh": sh, "g01": g01}
+
+    def smooth7(v):
+        for q in (2, 3, 5, 7):
+            while v % q == 0:
+                v //= q
+        return v == 1
+
+    fused2 = all(smooth7(n) for n in info["sizes"][2])
+    return {"L": sum(fd), "L01": fd[0] + fd[1], "sh": sh, "g01": g01, "fused2": fused2}
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the

@@ -153,6 +153,11 @@ CONFIGS = {
                periodic=(False, False, False), widths=8, t=8, tol=1e-5,
                medium=("grf", dict(mean=1.33, std=0.08, corr_len=6.0, seed=103)),
                source=("beam", dict(axis=2, index=16, waist=64.0))),
+    # C2 on an edge with a prime factor above 7 (subdomains of 123 = 3 x 41)
+    "C2P": dict(shape=(246, 246, 246), pixel=0.25, wavelength=1.0, split=(2, 2, 2),
+                periodic=(False, False, False), widths=8, t=8, tol=1e-5,
+                medium=("spheres", dict(count=40, r_range=(4, 20), n_range=(1.0, 1.6), seed=102, margin=8)),
+                source=("point", dict())),
     "C5": dict(shape=(1280, 1280, 1280), pixel=0.25, wavelength=1.0, split=(4, 4, 4),
                periodic=(False, False, False), widths=8, t=8, tol=1e-4,
                medium=("fill", dict(fill=0.30, r_range=(5, 40), n_range=(1.0, 1.5), seed=105, margin=8)),
