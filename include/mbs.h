@@ -151,6 +151,8 @@ typedef struct mbs_plan_info {
   int64_t sizes[3][MBS_MAX_SPLIT];  /* subdomain edges along each axis                        */
   size_t device_bytes;       /* device memory held by the plan                                 */
   int32_t graph_iters;
+  int32_t tma_groups;        /* axis-1 edge groups whose pass is fed by TMA (chosen at plan
+                                creation by timing both feeds; results are identical)          */
 } mbs_plan_info;
 
 MBS_API mbs_status mbs_plan_get_info(const mbs_plan *plan, mbs_plan_info *info);

@@ -44,7 +44,8 @@ class _Info(C.Structure):
     _fields_ = [("c_re", C.c_double), ("c_im", C.c_double), ("k0sq_re", C.c_double), ("k0sq_im", C.c_double),
                 ("contrast", C.c_double), ("block_norm", C.c_double), ("a", C.c_int32 * 3), ("t", C.c_int32),
                 ("alpha", C.c_double), ("shape", C.c_int64 * 3), ("split", C.c_int32 * 3),
-                ("sizes", (C.c_int64 * MAX_SPLIT) * 3), ("device_bytes", C.c_size_t), ("graph_iters", C.c_int32)]
+                ("sizes", (C.c_int64 * MAX_SPLIT) * 3), ("device_bytes", C.c_size_t), ("graph_iters", C.c_int32),
+                ("tma_groups", C.c_int32)]
 
 
 _lib = None
@@ -193,7 +194,7 @@ class Plan:
                     block_norm=inf.block_norm, a=list(inf.a), t=inf.t, alpha=inf.alpha, shape=tuple(inf.shape),
                     split=tuple(inf.split),
                     sizes=[list(inf.sizes[d][:inf.split[d]]) for d in range(3)], device_bytes=inf.device_bytes,
-                    graph_iters=inf.graph_iters)
+                    graph_iters=inf.graph_iters, tma_groups=inf.tma_groups)
 
     @staticmethod
     def workspace_bytes(shape, split, truncation=8, split_sizes=None, residual_form=False):

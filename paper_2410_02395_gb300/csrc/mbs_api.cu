@@ -646,6 +646,48 @@ cudaError_t strided_pass(const mbs_plan* p, const PassArgs& a, int n, bool inv) 
   return launch_strided(n, 1, inv, a, p->stream);
 }
 
+// Plan-time choice between the TMA-fed and the register-fed axis-1 pass of each
+// edge group: both run the same arithmetic (bit-identical results), so the
+// plan times both on its own geometry (forward and inverse, 2 warm-up and 5
+// timed launches each, CUDA events on the plan's stream; the FFT buffer's
+// contents do not matter) and keeps the tensor map only where TMA is faster.
+mbs_status autotune_strided(mbs_plan* p) {
+  if (p->tmaps.empty()) return MBS_OK;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  PassArgs a = base_args(p);
+  a.state = p->free_state;
+  std::vector<int> drop;
+  for (auto& gy : p->groups[1]) {
+    auto it = p->tmaps.find(1 * 65536 + gy.n);
+    if (it == p->tmaps.end()) continue;
+    a.nsub = gy.nsub;
+    memcpy(a.subs, gy.subs, sizeof(a.subs));
+    set_len_tables(p, a, gy.n);
+    float ms[2] = {0.f, 0.f};
+    for (int v = 0; v < 2; v++) {
+      auto launch = [&](bool inv) {
+        return v == 0 ? launch_strided_tma(gy.n, 1, inv, a, it->second, p->stream)
+                      : launch_strided(gy.n, 1, inv, a, p->stream);
+      };
+      for (int r = 0; r < 2; r++)
+        if (launch(false) || launch(true)) return fail(MBS_ECUDA, "axis-1 pass timing launch failed");
+      CU(cudaEventRecord(e0, p->stream));
+      for (int r = 0; r < 5; r++)
+        if (launch(false) || launch(true)) return fail(MBS_ECUDA, "axis-1 pass timing launch failed");
+      CU(cudaEventRecord(e1, p->stream));
+      CU(cudaEventSynchronize(e1));
+      CU(cudaEventElapsedTime(&ms[v], e0, e1));
+    }
+    if (ms[1] < ms[0]) drop.push_back(it->first);
+  }
+  for (int k : drop) p->tmaps.erase(k);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return MBS_OK;
+}
+
 // The forward half shared by the iteration and several operators:
 // rows_first (mode), strided axis-1 forward, mid (mode), strided axis-1 inverse.
 cudaError_t run_transform_chain(mbs_plan* p, PassArgs a, int first_mode, int mid_mode, Recorder* rec) {
@@ -970,6 +1012,8 @@ mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double p
   if (cudaMemcpyAsync(p->free_state, &fs, sizeof(fs), cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
       cudaStreamSynchronize(p->stream) != cudaSuccess)
     return cleanup(fail(MBS_ECUDA, "state init failed"));
+  st = autotune_strided(p);
+  if (st) return cleanup(st);
   *plan_out = p;
   return MBS_OK;
 }
@@ -993,6 +1037,7 @@ mbs_status mbs_plan_get_info(const mbs_plan* p, mbs_plan_info* info) {
     info->split[d] = p->S[d];
     for (int s = 0; s < p->S[d]; s++) info->sizes[d][s] = p->sizes[d][s];
   }
+  info->tma_groups = (int32_t)p->tmaps.size();
   return MBS_OK;
 }
 
