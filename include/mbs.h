@@ -81,7 +81,10 @@ typedef enum mbs_operator {
 /* Option flags. */
 #define MBS_FLAG_NO_GRAPH (1u << 0)  /* launch kernels one by one instead of replaying a CUDA graph */
 #define MBS_FLAG_CORR_TF32 (1u << 1) /* edge-correction contractions on the tensor cores as 3xTF32 with
-                                        FP32 accumulation (mma.sync m16n8k8); needs every corrected
+                                        FP32 accumulation (mma.sync m16n8k8): the separate correction
+                                        launches (axes 0 and 1 in the iteration, all axes in the
+                                        operators); the axis-2 terms the iteration fuses into its
+                                        first pass and layer update stay FP32. Needs every corrected
                                         subdomain edge >= 2t. Default: FP32 CUDA-core products.   */
 #define MBS_FLAG_RESIDUAL_FORM (1u << 2) /* iterate on r'_n = Gamma^-1 (A x_n - y) instead of x_n:
                                         r'_{n+1} = r'_n - alpha Gamma^-1 A r'_n, x_{n+1} = x_n - alpha r'_n

@@ -521,9 +521,9 @@ mbs_status setup_medium(mbs_plan* p, const float2* n_dev) {
   return MBS_OK;
 }
 
-// The first pass computes the axis-2 corrections of x itself unless they run on
-// the tensor cores or an axis-2 edge takes the Bluestein kernels.
-bool fuse_e2(const mbs_plan* p) { return !(p->flags & MBS_FLAG_CORR_TF32) && !p->bl_axis2; }
+// The first pass computes the axis-2 corrections of x itself (FP32, also in the
+// tensor-core form) unless an axis-2 edge takes the Bluestein kernels.
+bool fuse_e2(const mbs_plan* p) { return !p->bl_axis2; }
 
 // Twiddles (and Bluestein tables) of the transform of edge n.
 void set_len_tables(const mbs_plan* p, PassArgs& a, int n) {
@@ -574,10 +574,10 @@ ShellArgs shell_args(mbs_plan* p) {
 }
 
 // The iteration's layer update computes the axis-2 corrections of e itself
-// (one launch and one pass over the axis-2 layers less) unless the corrections
-// run on the tensor cores or the axis-2 split has too many layer voxels per row.
+// (one launch and one pass over the axis-2 layers less; FP32, also in the
+// tensor-core form) unless the axis-2 split has too many layer voxels per row.
 bool fused_layer_update(const mbs_plan* p) {
-  return !(p->flags & MBS_FLAG_CORR_TF32) && shell_rows_supported(p->g);
+  return shell_rows_supported(p->g);
 }
 
 // Edge corrections E F into the buffer C at the boundary-layer voxels.
@@ -615,7 +615,6 @@ cudaError_t run_corr_rec(mbs_plan* p, const float2* F, float2* C, const DevState
   c.C = C;
   c.c = make_float2((float)p->c_re, (float)p->c_im);
   c.tc = (p->flags & MBS_FLAG_CORR_TF32) ? 1 : 0;
-  if (c.tc) axis2 = true;  // no fused axis-2 path in the tensor-core form
   c.cW = p->cW;
   c.tb = p->tb;
   c.g = p->g;
