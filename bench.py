@@ -97,6 +97,22 @@ def layer_fractions(info):
 MEASURED_TRAFFIC = {("C2", "rows_last"): 509084160, ("C2", "rows_first"): 418301696}
 
 
+def max_over_ranks(x, ws, device=None):
+    """The largest x over the ranks: the job's time is its slowest rank's."""
+    if ws <= 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, seconds):
+    """Units processed by all ranks (replicas of the same work) per second of the slowest rank."""
+    return units_per_rank * ws / seconds
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -262,8 +278,8 @@ def run_batch(args, pkg, torch, ws, rank, dev):
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    value = vox * K * ws / (ms / 1e3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
+    value = whole_job_rate(vox * K, ws, ms / 1e3)
     # the same solves one after another, each with its own graph replays
     t0 = time.perf_counter()
     for p in plans:
@@ -376,13 +392,10 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         clk = clocks.stop()
-        ms = ev0.elapsed_time(ev1)
+        ms = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
         if ws > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
             torch.distributed.barrier()
-        value = vox * K * ws / (ms / 1e3)
+        value = whole_job_rate(vox * K, ws, ms / 1e3)
 
         # ---- per-kernel CUDA-event timing (same workload, kernels launched one by one)
         prof = plan.profile(K)
@@ -414,12 +427,8 @@ def main():
             t0 = time.perf_counter()
             for _ in range(args.e2e_steps):
                 plan.solve(hsrc, tol=0.0, max_iter=args.e2e_iters, out=hout)
-            dt = time.perf_counter() - t0
-            if ws > 1:
-                tt = torch.tensor([dt], device=dev)
-                torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-                dt = float(tt.item())
-            e2e = {"value": vox * args.e2e_iters * args.e2e_steps * ws / dt, "unit": UNIT,
+            dt = max_over_ranks(time.perf_counter() - t0, ws, dev)
+            e2e = {"value": whole_job_rate(vox * args.e2e_iters * args.e2e_steps, ws, dt), "unit": UNIT,
                    "h2d_bytes_per_step": vox * 8, "d2h_bytes_per_step": vox * 8 + 8 * args.e2e_iters,
                    "step": "one mbs_solve call: pinned host source -> device, %d iterations, field -> pinned host"
                            % args.e2e_iters}
@@ -442,13 +451,9 @@ def main():
             pm.iterate(K, 0.0, no_poll=True)
             ev1.record(stream)
             torch.cuda.synchronize(dev)
-            msm = ev0.elapsed_time(ev1)
-            if ws > 1:
-                tm = torch.tensor([msm], device=dev)
-                torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
-                msm = float(tm.item())
+            msm = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
             pm.close()
-            mixed = {"value": vox * K * ws / (msm / 1e3), "unit": UNIT, "ms_per_step": msm / K,
+            mixed = {"value": whole_job_rate(vox * K, ws, msm / 1e3), "unit": UNIT, "ms_per_step": msm / K,
                      "corrections": "3xTF32 mma.sync m16n8k8, FP32 accumulate"}
 
         # ---- time to tolerance (residual form: no complex64 floor) -----------
