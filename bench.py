@@ -456,6 +456,24 @@ def main():
             mixed = {"value": whole_job_rate(vox * K, ws, msm / 1e3), "unit": UNIT, "ms_per_step": msm / K,
                      "corrections": "3xTF32 mma.sync m16n8k8, FP32 accumulate"}
 
+        # ---- the same iterations launched kernel by kernel from the host -----
+        # (no CUDA graph: one launch per pass and iteration, host launch cost included)
+        Kn = max(10, K // 10)
+        pn = pkg.Plan(shape, params["pixel"], params["wavelength"], n_dev, no_graph=True, **kw)
+        pn.set_source(src_dev)
+        pn.iterate(max(args.warmup, 3), 0.0, no_poll=True)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        pn.iterate(Kn, 0.0, no_poll=True)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        msn = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
+        pn.close()
+        no_graph = {"value": whole_job_rate(vox * Kn, ws, msn / 1e3), "unit": UNIT, "ms_per_step": msn / Kn,
+                    "steps": Kn, "how": "same kernels, launched one by one from the host (MBS_FLAG_NO_GRAPH)"}
+
         # ---- time to tolerance (residual form: no complex64 floor) -----------
         ttt_line = None
         if not args.no_ttt:
@@ -512,6 +530,7 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "mixed": mixed,
+            "no_graph": no_graph,
             "time_to_tol": ttt_line,
         }
         if args.t_sweep:
