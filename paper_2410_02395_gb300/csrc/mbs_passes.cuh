@@ -4,7 +4,9 @@
 //               source and edge corrections of V, Sec. 3.1 steps 3-5) into the
 //               coalesced staged load.
 //   strided     axis-1 forward / inverse transform (global loads straight into
-//               the first radix stage, global stores from the last).
+//               the first radix stage, global stores from the last); the
+//               TMA-fed form of this pass is in mbs_tma.cuh, the Bluestein
+//               forms of all four passes in mbs_bluestein.cuh.
 //   mid         axis-0 forward transform, k-space multiplier, axis-0 inverse
 //               transform in one pass; the multiplier is the propagator
 //               1/(c(k0^2 - |p|^2) + 1) (or the symbol of L), both scaled by
