@@ -143,16 +143,26 @@ __global__ void __launch_bounds__(128) k_corr_side(const __grid_constant__ CorrA
     const float2 v = nb >= 0 ? F[nb0 + (long long)b * stride] : make_float2(0.f, 0.f);
     G[b] = csub(v, o);
   }
-  float2 w[2 * T - 1];
-  load_toeplitz<T>(a.cW, w);
+  // c is purely imaginary and W real: c W = i w with w = Im(c W) (2t - 1 distinct
+  // values along the diagonals), so sum_b cW_b G_b = i v with v = sum_b w_b G_b.
+  float w[2 * T - 1];
+#pragma unroll
+  for (int m = 0; m < 2 * T - 1; m++) {
+    const int aa = m < T - 1 ? T - 1 - m : 0, bb = aa + m - (T - 1);
+    w[m] = __ldg(&a.cW[aa * T + bb].y);
+  }
   float2* C = a.C;
   const long long out0 = base + (long long)(side ? off + n - T : off) * stride;
 #pragma unroll
   for (int q = 0; q < T; q++) {
-    float2 v = make_float2(0.f, 0.f);
+    float vx = 0.f, vy = 0.f;
 #pragma unroll
-    for (int b = 0; b < T; b++) v = cadd(v, cmul(side ? w[b - q + T - 1] : w[q - b + T - 1], G[b]));
-    put(C, out0 + (long long)q * stride, v, add);
+    for (int b = 0; b < T; b++) {
+      const float wb = side ? w[b - q + T - 1] : w[q - b + T - 1];
+      vx = fmaf(wb, G[b].x, vx);
+      vy = fmaf(wb, G[b].y, vy);
+    }
+    put(C, out0 + (long long)q * stride, make_float2(-vy, vx), add);
   }
 }
 
