@@ -24,18 +24,21 @@ __device__ __forceinline__ void put(float2* C, long long v, float2 val, bool add
   C[v] = add ? cadd(C[v], val) : val;
 }
 
-// W is Toeplitz, W[a][b] = D(t + b - a): its 2t - 1 distinct entries c*D(1..2t-1)
-// are cw[m] = cW[0][m - t + 1]... indexed here by b - a + t - 1.
+// W is Toeplitz, W[a][b] = D(t + b - a): 2t - 1 distinct entries, indexed here
+// by m = b - a + t - 1 (row a = max(0, t - 1 - m), column b = a + m - (t - 1)).
+// c is purely imaginary (Eq. c_scale2) and W real, so c W = i w with
+// w = Im(c W) real and sum_b cW_b f_b = i v with v = sum_b w_b f_b (two FMAs per
+// term); load_toeplitz_im returns the 2t - 1 values of w.
 template <int T>
-__device__ __forceinline__ void load_toeplitz(const float2* __restrict__ cW, float2 (&w)[2 * T - 1]) {
+__device__ __forceinline__ void load_toeplitz_im(const float2* __restrict__ cW, float (&w)[2 * T - 1]) {
 #pragma unroll
   for (int m = 0; m < 2 * T - 1; m++) {
-    // b - a = m - (T - 1): take row a = max(0, T-1-m), column b = a + m - (T - 1)
     const int aa = m < T - 1 ? T - 1 - m : 0;
     const int bb = aa + m - (T - 1);
-    w[m] = __ldg(cW + aa * T + bb);
+    w[m] = __ldg(&cW[aa * T + bb].y);
   }
 }
+__device__ __forceinline__ float2 times_i(float vx, float vy) { return make_float2(-vy, vx); }
 
 // Axes 0 and 1: one thread per (pencil, subdomain); consecutive threads take
 // consecutive axis-2 positions, so every load and store is coalesced.
@@ -74,24 +77,31 @@ __global__ void __launch_bounds__(128) k_corr_strided(const __grid_constant__ Co
     D[b] = csub(Rv, A);
     E[b] = csub(Lv, Z);
   }
-  float2 w[2 * T - 1];
-  load_toeplitz<T>(a.cW, w);
+  float w[2 * T - 1];
+  load_toeplitz_im<T>(a.cW, w);
   float2* C = a.C;
   // first t layers: (W^T E)[q] = sum_b W[b][q] E[b] = sum_b w[q - b + T - 1] E[b]
   float2 outf[T];
 #pragma unroll
   for (int q = 0; q < T; q++) {
-    float2 v = make_float2(0.f, 0.f);
+    float vx = 0.f, vy = 0.f;
 #pragma unroll
-    for (int b = 0; b < T; b++) v = cadd(v, cmul(w[q - b + T - 1], E[b]));
-    outf[q] = v;
+    for (int b = 0; b < T; b++) {
+      vx = fmaf(w[q - b + T - 1], E[b].x, vx);
+      vy = fmaf(w[q - b + T - 1], E[b].y, vy);
+    }
+    outf[q] = times_i(vx, vy);
   }
   // last t layers: (W D)[aa] = sum_b W[aa][b] D[b] = sum_b w[b - aa + T - 1] D[b]
 #pragma unroll
   for (int aa = 0; aa < T; aa++) {
-    float2 v = make_float2(0.f, 0.f);
+    float vx = 0.f, vy = 0.f;
 #pragma unroll
-    for (int b = 0; b < T; b++) v = cadd(v, cmul(w[b - aa + T - 1], D[b]));
+    for (int b = 0; b < T; b++) {
+      vx = fmaf(w[b - aa + T - 1], D[b].x, vx);
+      vy = fmaf(w[b - aa + T - 1], D[b].y, vy);
+    }
+    const float2 v = times_i(vx, vy);
     const int q = n - T + aa;
     if (q < T) {
       outf[q] = cadd(outf[q], v);  // n < 2t: the voxel is in both ranges (q == n - T + aa)
@@ -143,14 +153,8 @@ __global__ void __launch_bounds__(128) k_corr_side(const __grid_constant__ CorrA
     const float2 v = nb >= 0 ? F[nb0 + (long long)b * stride] : make_float2(0.f, 0.f);
     G[b] = csub(v, o);
   }
-  // c is purely imaginary and W real: c W = i w with w = Im(c W) (2t - 1 distinct
-  // values along the diagonals), so sum_b cW_b G_b = i v with v = sum_b w_b G_b.
   float w[2 * T - 1];
-#pragma unroll
-  for (int m = 0; m < 2 * T - 1; m++) {
-    const int aa = m < T - 1 ? T - 1 - m : 0, bb = aa + m - (T - 1);
-    w[m] = __ldg(&a.cW[aa * T + bb].y);
-  }
+  load_toeplitz_im<T>(a.cW, w);
   float2* C = a.C;
   const long long out0 = base + (long long)(side ? off + n - T : off) * stride;
 #pragma unroll
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(128) k_corr_side(const __grid_constant__ CorrA
       vx = fmaf(wb, G[b].x, vx);
       vy = fmaf(wb, G[b].y, vy);
     }
-    put(C, out0 + (long long)q * stride, make_float2(-vy, vx), add);
+    put(C, out0 + (long long)q * stride, times_i(vx, vy), add);
   }
 }
 
@@ -179,10 +183,10 @@ __global__ void __launch_bounds__(256) k_corr_rows(const __grid_constant__ CorrA
   float2* sm = cs + warp * M;
   const long long N1 = a.g.N1, N2 = a.g.N2, rows = a.g.N0 * N1;
   const float2* __restrict__ F = a.F;
-  __shared__ float2 w[2 * T - 1];  // lanes index it with their own (runtime) output position
+  __shared__ float w[2 * T - 1];  // lanes index it with their own (runtime) output position
   if (threadIdx.x == 0) {
-    float2 wr[2 * T - 1];
-    load_toeplitz<T>(a.cW, wr);
+    float wr[2 * T - 1];
+    load_toeplitz_im<T>(a.cW, wr);
 #pragma unroll
     for (int m = 0; m < 2 * T - 1; m++) w[m] = wr[m];
   }
@@ -207,13 +211,14 @@ __global__ void __launch_bounds__(256) k_corr_rows(const __grid_constant__ CorrA
       // in the first range (n < 2t) are produced by the first-range lane
       const int q = k < T ? k : n - T + (k - T);
       if (k >= T && q < T) continue;
-      float2 v = make_float2(0.f, 0.f);
+      float vx = 0.f, vy = 0.f;
       if (q < T) {  // first t layers: row q of W^T on (left's last t - own last t)
 #pragma unroll
         for (int b = 0; b < T; b++) {
           float2 f = make_float2(-own[T + b].x, -own[T + b].y);
           if (lft >= 0) f = cadd(f, sm[lft * 2 * T + T + b]);
-          v = cadd(v, cmul(w[q - b + T - 1], f));
+          vx = fmaf(w[q - b + T - 1], f.x, vx);
+          vy = fmaf(w[q - b + T - 1], f.y, vy);
         }
       }
       if (q >= n - T) {  // last t layers: row q-(n-t) of W on (right's first t - own first t)
@@ -222,10 +227,11 @@ __global__ void __launch_bounds__(256) k_corr_rows(const __grid_constant__ CorrA
         for (int b = 0; b < T; b++) {
           float2 f = make_float2(-own[b].x, -own[b].y);
           if (rgt >= 0) f = cadd(f, sm[rgt * 2 * T + b]);
-          v = cadd(v, cmul(w[b - aa + T - 1], f));
+          vx = fmaf(w[b - aa + T - 1], f.x, vx);
+          vy = fmaf(w[b - aa + T - 1], f.y, vy);
         }
       }
-      put(C, rb + ax.off[s] + q, v, add);
+      put(C, rb + ax.off[s] + q, times_i(vx, vy), add);
     }
     __syncwarp();
   }
