@@ -87,3 +87,23 @@ def test_edge_length_rule(lib):
             assert e.status == 8, (n, e.status)
             got = False
         assert got == ok, n
+
+
+def test_degenerate_and_limit_arguments(lib):
+    """Empty and out-of-range arguments are refused with a status, nothing runs."""
+    import paper_2410_02395_gb300 as pkg
+
+    def status(*args, **kw):
+        try:
+            pkg.Plan.workspace_bytes(*args, **kw)
+            return 0
+        except pkg.MBSError as e:
+            return e.status
+
+    assert status((0, 8, 8), (1, 1, 1)) == 1                 # empty grid
+    assert status((8, 8, 8), (1, 9, 1)) == 1                 # more subdomains than voxels along an axis
+    assert status((8, 8, 8), (1, 1, 1), truncation=33) == 1  # t above MBS_MAX_T
+    assert status((64, 8, 8), (2, 1, 1), truncation=17) == 8  # t not among the compiled widths
+    assert status((16 * 32, 8, 8), (16, 1, 1)) == 0          # MBS_MAX_SPLIT subdomains along an axis
+    assert status((512, 8, 8), (1, 1, 1)) == 0               # MBS_MAX_EDGE
+    assert status((1, 1, 1), (1, 1, 1), truncation=1) == 0   # a single voxel
