@@ -118,10 +118,10 @@ def test_planted_transposed_block_is_caught():
 
 @pytest.mark.parametrize("shape,t", [((1, 1, 1), 1), ((2, 2, 2), 2), ((3, 3, 3), 3)])
 def test_c_scale_bound_fails_when_layer_ranges_coincide(shape, t):
-    """Eq. c_scale2 bounds ||V|| by the norms of its parts, one ||W|| per a_d. When a
-    subdomain edge n is at most t, a voxel is in the first and the last t layers
-    at once and receives both wrap terms, so that bound no longer holds (reading
-    R15): the dense ||V|| exceeds 1 and the series diverges on such grids."""
+    """Eq. c_scale2 bounds ||V|| by the norms of its parts, one ||W|| per a_d. On an
+    unsplit grid whose edge n is at most t, a voxel is in the first and the last t
+    layers at once and receives both wrap terms, so that bound no longer holds
+    (reading R15): the dense ||V|| exceeds 1 and the series diverges there."""
     n = np.full(shape, 1.2 + 0.0j)
     p = Problem(n, 0.25, 1.0, split=(1, 1, 1), periodic=(False, False, False), t=t)
     L = dr.dense_L(p.shape, p.sizes, p.h, p.k0sq, p.c)
