@@ -88,3 +88,35 @@ def test_decomposition_matches_single_domain_solution():
     e2 = relative_l2(x2, x1) ** 2
     e4 = relative_l2(x4, x1) ** 2
     assert e2 < 1e-3 and e4 < 1e-3      # squared metric of Sec. 4.1
+
+
+def test_green_function_3d():
+    """Lossy homogeneous medium (n = 1 + 0.05i), periodic 64^3 grid at lambda/4,
+    voxel source: away from the source the field equals the outgoing 3-D Green's
+    function h^3 exp(ikr)/(4 pi r) (reading R10), summed over the nearest periodic
+    images (the loss makes farther ones negligible). The remaining difference is the
+    band limit of the grid (the source is a band-limited delta)."""
+    N, h, lam, loss = 64, 0.25, 1.0, 0.05
+    n = np.full((N, N, N), 1.0 + loss * 1j)
+    p = Problem(n, h, lam, periodic=(True, True, True))
+    S = np.zeros((N, N, N), dtype=complex)
+    c = N // 2
+    S[c, c, c] = 1.0
+    x, iters, _ = p.solve(S, tol=1e-10, max_iter=2000)
+    assert iters < 2000
+    k = 2 * np.pi * (1.0 + loss * 1j) / lam
+    Lbox = N * h
+    ax = (np.arange(N) - c) * h
+    X, Y, Z = np.meshgrid(ax, ax, ax, indexing="ij")
+    G = np.zeros((N, N, N), dtype=complex)
+    for mx in (-1, 0, 1):
+        for my in (-1, 0, 1):
+            for mz in (-1, 0, 1):
+                r = np.sqrt((X + mx * Lbox) ** 2 + (Y + my * Lbox) ** 2 + (Z + mz * Lbox) ** 2)
+                r[r == 0] = np.inf
+                G += np.exp(1j * k * r) / (4 * np.pi * r)
+    G *= h ** 3
+    R = np.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+    for lo, hi in ((1.0, 2.0), (2.0, 4.0), (4.0, 6.0)):   # shells in wavelengths
+        sel = (R >= lo) & (R <= hi)
+        assert relative_l2(x[sel], G[sel]) < 1.5e-2
