@@ -1,6 +1,7 @@
 """The C-ABI library builds, loads and exports every symbol include/mbs.h declares
 (no compute calls: this runs without a GPU)."""
 import ctypes
+import ctypes as C
 import os
 import re
 
@@ -107,3 +108,32 @@ def test_degenerate_and_limit_arguments(lib):
     assert status((16 * 32, 8, 8), (16, 1, 1)) == 0          # MBS_MAX_SPLIT subdomains along an axis
     assert status((512, 8, 8), (1, 1, 1)) == 0               # MBS_MAX_EDGE
     assert status((1, 1, 1), (1, 1, 1), truncation=1) == 0   # a single voxel
+
+
+def test_host_only_entry_points(lib):
+    """Defaults, kernel-kind names and error text need no device."""
+    import paper_2410_02395_gb300 as pkg
+
+    opts = pkg._Options()
+    lib.mbs_default_options(C.byref(opts))
+    assert opts.truncation == 8 and opts.alpha == 0.75 and opts.absorb_kappa == 0.5
+    assert opts.flags == 0 and opts.periodic_mask == 0 and not opts.split_sizes
+    lib.mbs_kernel_kind_name.restype = C.c_char_p
+    names = [lib.mbs_kernel_kind_name(k).decode() for k in range(pkg.KERNEL_KINDS)]
+    assert names == ["corr_x", "rows_first", "strided_fwd", "mid_axis0", "strided_inv", "rows_last", "corr_e",
+                     "shell_update"]
+    assert lib.mbs_kernel_kind_name(pkg.KERNEL_KINDS) == b""
+    with pytest.raises(pkg.MBSError) as ei:
+        pkg.Plan.workspace_bytes((8, 8, 262), (1, 1, 1))     # 262 = 2 x 131: no FFT for it
+    lib.mbs_last_error.restype = C.c_char_p
+    assert ei.value.status == 8 and b"262" in lib.mbs_last_error()
+
+
+def test_workspace_grows_with_the_grid_and_the_residual_form(lib):
+    import paper_2410_02395_gb300 as pkg
+
+    b64 = pkg.Plan.workspace_bytes((64, 64, 64), (1, 1, 1))
+    b128 = pkg.Plan.workspace_bytes((128, 64, 64), (2, 1, 1))
+    assert b128 > 2 * b64 * 0.9
+    br = pkg.Plan.workspace_bytes((64, 64, 64), (1, 1, 1), residual_form=True)
+    assert br - b64 >= 64 ** 3 * 12   # r' (8 B) and the low word of x (4 B) per voxel
