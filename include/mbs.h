@@ -96,6 +96,9 @@ typedef enum mbs_operator {
                                      of tensor-map (TMA) copies into double-buffered shared memory.
                                      Default: TMA where the edge has TMA kernels (32, 64, 128, 256)
                                      and the grid's row pitch is a multiple of 16 bytes.          */
+#define MBS_FLAG_FORCE_TMA (1u << 4) /* keep every tensor-map feed the plan can build instead of timing
+                                     the TMA-fed against the register-fed axis-1 pass at plan
+                                     creation and keeping the faster (results are identical)      */
 
 typedef struct mbs_options {
   int32_t truncation;        /* t, the kept edge width (Sec. 3, Fig. 5); 0 -> 8 (Sec. 3.3)      */
@@ -111,6 +114,10 @@ typedef struct mbs_options {
   void *workspace;           /* optional device workspace of workspace_bytes (see
                                 mbs_workspace_bytes); NULL -> the plan allocates its own          */
   size_t workspace_bytes;
+  int64_t tma_wait_cycles;   /* bound of each wait for a tensor-map copy in the iteration and the
+                                operators, in SM clock cycles; 0 -> about 2 s. Past it the call
+                                returns MBS_ETIMEOUT (a short bound lets a test provoke that path
+                                with copies that do complete)                                     */
 } mbs_options;
 
 /* Fill *opts with the defaults above. */
@@ -227,14 +234,19 @@ MBS_API const char *mbs_kernel_kind_name(int32_t kind);
  * memory budget: mbs_apply_operator may allocate staging buffers on first use.
  * Here the correction scratch is a fixed 16 MiB array inside the library (every
  * GPU that loads the library holds it until the process exits), the plan's own
- * buffers are not touched, and nothing is allocated on any path.
- *  - x and out: device pointers only (complex64, the plan's grid); host pointers
- *    are rejected with MBS_EINVAL because they would need a staging buffer.
+ * buffers are not touched, and the call allocates nothing.
+ *  - x and out: device pointers on the plan's device only (complex64, the plan's
+ *    grid); host pointers are rejected with MBS_EINVAL because they would need a
+ *    staging buffer, and so are pointers on another device. The plan's device
+ *    must be current.
  *  - grids above 2^21 voxels (the scratch's capacity) are rejected with MBS_EINVAL.
- *  - The first call on a device looks up the scratch's device address with that
- *    device current; make that first call before any stream capture.
+ *  - The scratch's device address is looked up once per device, with that
+ *    device current: mbs_plan_create does it for the plan's device (loading the
+ *    library's module that holds the array); if that failed, the first call here
+ *    does it and should then come before any stream capture.
  *  - All calls share the scratch: calls whose work overlaps on the GPU (on
- *    different streams or plans) race. Runs on the plan's stream, synchronous.
+ *    different streams or plans) race. The work runs on the plan's stream and the
+ *    call synchronises that stream before it returns.
  *  - Errors: mbs_noalloc_last_error() describes the last failure of this call.
  */
 MBS_API mbs_status mbs_apply_edge_corrections_noalloc(const mbs_plan *plan, const void *x, void *out);

@@ -37,7 +37,7 @@ class _Options(C.Structure):
     _fields_ = [("truncation", C.c_int32), ("alpha", C.c_double), ("periodic_mask", C.c_uint32),
                 ("absorb_kappa", C.c_double), ("split_sizes", C.POINTER(C.c_int64)), ("flags", C.c_uint32),
                 ("graph_iters", C.c_int32), ("stream", C.c_void_p), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t)]
+                ("workspace_bytes", C.c_size_t), ("tma_wait_cycles", C.c_int64)]
 
 
 class _Info(C.Structure):
@@ -153,7 +153,7 @@ class Plan:
     def __init__(self, shape, pixel_size, wavelength, refractive_index, boundary_widths=((0, 0),) * 3,
                  split=(1, 1, 1), truncation=8, alpha=0.75, periodic=(False, False, False), kappa=0.5,
                  split_sizes=None, graph_iters=0, no_graph=False, corr_tf32=False, residual_form=False,
-                 no_tma=False, stream=None, workspace=None):
+                 no_tma=False, force_tma=False, tma_wait_cycles=0, stream=None, workspace=None):
         self.lib = load_library()
         self.shape = tuple(int(s) for s in shape)
         opts = _Options()
@@ -164,7 +164,8 @@ class Plan:
         opts.absorb_kappa = float(kappa)
         opts.graph_iters = int(graph_iters)
         opts.flags = (1 if no_graph else 0) | (2 if corr_tf32 else 0) | (4 if residual_form else 0) | \
-            (8 if no_tma else 0)
+            (8 if no_tma else 0) | (16 if force_tma else 0)
+        opts.tma_wait_cycles = int(tma_wait_cycles)
         self._split_sizes = None
         if split_sizes is not None:
             flat = [int(v) for d in range(3) for v in split_sizes[d]]

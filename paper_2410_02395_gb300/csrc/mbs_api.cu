@@ -117,7 +117,9 @@ struct mbs_plan {
   bool has_shell;
   uint32_t flags;
   int graph_iters;
+  long long tma_wait;  // bound of a TMA tile wait (SM cycles, 0: the kernels' default)
   // device
+  int device;
   cudaStream_t stream;
   bool own_stream;
   void* base;
@@ -288,6 +290,8 @@ mbs_status validate_and_fill(mbs_plan* p, const int64_t shape[3], double h, doub
   p->periodic = o ? o->periodic_mask : 0u;
   p->flags = o ? o->flags : 0u;
   p->graph_iters = (o && o->graph_iters > 0) ? o->graph_iters : 0;
+  if (o && o->tma_wait_cycles < 0) return fail(MBS_EINVAL, "tma_wait_cycles must be >= 0");
+  p->tma_wait = o ? (long long)o->tma_wait_cycles : 0;
   int k = 0;
   for (int d = 0; d < 3; d++) {
     if (shape[d] < 1 || shape[d] > (1 << 20)) return fail(MBS_EINVAL, "grid extents must be in [1, 2^20]");
@@ -556,6 +560,7 @@ PassArgs base_args(mbs_plan* p) {
   a.fuse_e2 = fuse_e2(p) ? 1 : 0;
   a.tb = p->tb;
   a.g = p->g;
+  a.tma_wait = p->tma_wait;
   return a;
 }
 
@@ -651,12 +656,13 @@ cudaError_t strided_pass(const mbs_plan* p, const PassArgs& a, int n, bool inv) 
 // timed launches each, CUDA events on the plan's stream; the FFT buffer's
 // contents do not matter) and keeps the tensor map only where TMA is faster.
 mbs_status autotune_strided(mbs_plan* p) {
-  if (p->tmaps.empty()) return MBS_OK;
+  if (p->tmaps.empty() || (p->flags & MBS_FLAG_FORCE_TMA)) return MBS_OK;
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   PassArgs a = base_args(p);
   a.state = p->free_state;
+  a.tma_wait = 0;  // the full bound: a caller's short bound is for the iteration and the operators
   std::vector<int> drop;
   for (auto& gy : p->groups[1]) {
     auto it = p->tmaps.find(1 * 65536 + gy.n);
@@ -876,6 +882,30 @@ mbs_status stage_in(mbs_plan* p, const void* src, float2** dev_out, float2** scr
   return MBS_OK;
 }
 
+// The operator state: zero (never done, no status).
+cudaError_t clear_free_state(mbs_plan* p) {
+  DevState fs;
+  memset(&fs, 0, sizeof(fs));
+  cudaError_t e = cudaMemcpyAsync(p->free_state, &fs, sizeof(fs), cudaMemcpyHostToDevice, p->stream);
+  if (!e) e = cudaStreamSynchronize(p->stream);
+  return e;
+}
+
+// After an operator's work has finished: a bounded wait that expired marks the
+// operator state done (every later kernel of the call left at once), so the
+// output is incomplete. Report that and re-arm the state for later calls.
+mbs_status check_free_state(mbs_plan* p) {
+  DevState hs;
+  CU(cudaMemcpyAsync(p->host_state, p->free_state, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  hs = *p->host_state;
+  if (hs.done || hs.status) {
+    CU(clear_free_state(p));
+    return fail(MBS_ETIMEOUT, "a bounded wait for a tensor-map copy expired; the output is incomplete");
+  }
+  return MBS_OK;
+}
+
 }  // namespace
 
 bool mbs_plan_corr_view(const mbs_plan* p, CorrView* v) {
@@ -887,7 +917,7 @@ bool mbs_plan_corr_view(const mbs_plan* p, CorrView* v) {
   v->tc = (p->flags & MBS_FLAG_CORR_TF32) ? 1 : 0;
   v->has_shell = p->has_shell;
   v->nvox = nvox(p);
-  v->free_state = p->free_state;
+  v->device = p->device;
   v->stream = p->stream;
   return true;
 }
@@ -928,6 +958,11 @@ mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double p
     return fail(MBS_ECUDA, "no CUDA device");
   }
   mbs_plan* p = new mbs_plan();
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return fail(MBS_ECUDA, "no current device");
+  }
   p->stream = nullptr;
   p->own_stream = false;
   p->base = nullptr;
@@ -1005,14 +1040,14 @@ mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double p
   if (launch_state_arm(p->state, 0, 0.0, 1, kHistCap, p->stream) ||
       launch_state_arm(p->free_state, 0, 0.0, 1, kHistCap, p->stream))
     return cleanup(fail(MBS_ECUDA, "state init failed"));
-  // the operator state is never "done"
-  DevState fs;
-  memset(&fs, 0, sizeof(fs));
-  if (cudaMemcpyAsync(p->free_state, &fs, sizeof(fs), cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
-      cudaStreamSynchronize(p->stream) != cudaSuccess)
-    return cleanup(fail(MBS_ECUDA, "state init failed"));
   st = autotune_strided(p);
   if (st) return cleanup(st);
+  // the allocation-free correction entry's scratch address on this device (its
+  // first use would otherwise load the module that holds it); a failure here
+  // only means that entry point looks it up again when first called
+  noalloc_prepare_current_device();
+  // the operator state is never "done" (its status records a bounded wait that expired)
+  if (clear_free_state(p)) return cleanup(fail(MBS_ECUDA, "state init failed"));
   *plan_out = p;
   return MBS_OK;
 }
@@ -1141,7 +1176,7 @@ mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* o
   if (e) return fail(MBS_ECUDA, std::string("operator launch: ") + cudaGetErrorString(e));
   if (!out_dev) CU(cudaMemcpyAsync(out, od, nv * sizeof(float2), cudaMemcpyDeviceToHost, p->stream));
   CU(cudaStreamSynchronize(p->stream));
-  return MBS_OK;
+  return check_free_state(p);
 }
 
 mbs_status mbs_set_source(mbs_plan* p, const void* source) {

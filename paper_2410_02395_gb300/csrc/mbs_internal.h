@@ -98,6 +98,7 @@ struct PassArgs {
   int mode;
   int nsub;             // subdomains (along the pass axis) of this size
   int subs[kMaxSplit];
+  long long tma_wait;   // bound of a TMA tile wait in SM clock cycles (0: about 2 s)
 };
 
 // Edge corrections E_d F of one axis, written (or, where an earlier axis has
@@ -187,9 +188,14 @@ struct CorrView {
   int tc;
   bool has_shell;
   int64_t nvox;
-  const DevState* free_state;
+  int device;            // the device the plan's buffers and stream belong to
   cudaStream_t stream;
 };
+
+// Looks up, with the current device, the device address of the fixed scratch
+// of mbs_apply_edge_corrections_noalloc (once per device; mbs_plan_create calls
+// it for the plan's device). False if the lookup failed.
+bool noalloc_prepare_current_device();
 
 }  // namespace mbs
 

@@ -35,16 +35,45 @@ mbs_status nfail(mbs_status s, const std::string& m) {
   return s;
 }
 
-bool on_device(const void* p) {
+// The device a pointer's memory lives on, or -1 for host (or unknown) memory.
+int device_of(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return -1;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? at.device : -1;
+}
+
+// Device address of the scratch on the current device `dev` (looked up once).
+float2* scratch_on(int dev, cudaError_t* err) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_corr_scratch);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *err = e;
+      return nullptr;
+    }
+    g_addr[dev] = (float2*)p;
+  }
+  return g_addr[dev];
 }
 
 }  // namespace
+
+namespace mbs {
+bool noalloc_prepare_current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaError_t e = cudaSuccess;
+  return scratch_on(dev, &e) != nullptr;
+}
+}  // namespace mbs
 
 extern "C" {
 
@@ -55,31 +84,33 @@ mbs_status mbs_apply_edge_corrections_noalloc(const mbs_plan* plan, const void* 
   mbs::CorrView v;
   if (!plan || !x || !out || !mbs_plan_corr_view(plan, &v)) return nfail(MBS_EINVAL, "null argument");
   if (x == out) return nfail(MBS_EINVAL, "x and out must not alias");
-  if (!on_device(x) || !on_device(out))
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return nfail(MBS_ECUDA, "no usable current device");
+  }
+  if (dev != v.device)
+    return nfail(MBS_EINVAL, "the current device (" + std::to_string(dev) + ") is not the plan's device (" +
+                                 std::to_string(v.device) + ")");
+  const int dx = device_of(x), dout = device_of(out);
+  if (dx < 0 || dout < 0)
     return nfail(MBS_EINVAL, "x and out must be device pointers (host data would need a staging allocation)");
+  if (dx != v.device || dout != v.device) return nfail(MBS_EINVAL, "x and out must be on the plan's device");
   if (v.nvox > kNoAllocMaxVoxels)
     return nfail(MBS_EINVAL, "grid of " + std::to_string(v.nvox) + " voxels exceeds the " +
                                  std::to_string(kNoAllocMaxVoxels) + "-voxel scratch of this entry point");
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return nfail(MBS_ECUDA, "no usable current device");
-  float2* scratch = nullptr;
-  {
-    // once per device, with that device current: the device address of the array
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_corr_scratch);
-      if (e != cudaSuccess) return nfail(MBS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_addr[dev] = (float2*)p;
-    }
-    scratch = g_addr[dev];
-  }
+  // normally found when the plan was created on this device
+  cudaError_t le = cudaSuccess;
+  float2* scratch = scratch_on(dev, &le);
+  if (!scratch) return nfail(MBS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(le));
   float2* o = (float2*)out;
   cudaError_t e = mbs::launch_zero(o, v.nvox, v.stream);
   if (!e && v.has_shell) {
-    // every boundary-layer voxel of the scratch is written by the first axis
-    // that covers it before it is read, so nothing needs clearing
+    // Every boundary-layer voxel of the scratch is written (not added) by the
+    // first corrected axis whose layers hold it, before any axis adds to it or
+    // the final kernel reads it, so what an earlier call left there is never
+    // read and nothing needs clearing. No solver state is passed (null): these
+    // kernels never leave early.
     mbs::CorrArgs c = {};
     c.F = (const float2*)x;
     c.C = scratch;
@@ -88,7 +119,7 @@ mbs_status mbs_apply_edge_corrections_noalloc(const mbs_plan* plan, const void* 
     c.tc = v.tc;
     c.tb = v.tb;
     c.g = v.g;
-    c.state = v.free_state;
+    c.state = nullptr;
     for (int d = 0; d < 3 && !e; d++) {
       if (v.g.ax[d].a <= 0) continue;
       c.axis = d;
@@ -100,7 +131,7 @@ mbs_status mbs_apply_edge_corrections_noalloc(const mbs_plan* plan, const void* 
       s.out = o;
       s.tb = v.tb;
       s.g = v.g;
-      s.state = v.free_state;
+      s.state = nullptr;
       s.mode = mbs::SHELL_SET_E;
       e = mbs::launch_shell(s, 152 * 8, v.stream);
     }

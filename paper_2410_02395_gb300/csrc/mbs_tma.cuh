@@ -7,9 +7,13 @@
 // (row e = element e of the 32 pencils; positions past N2 read as zeros).
 // Persistent CTAs walk the tiles with two buffers: the copy of the next tile
 // is in flight while the current one is transformed in place; the last radix
-// stage stores straight to global memory. Every wait on an mbarrier is bounded:
-// past the limit the kernel marks the solver state (MBS_ETIMEOUT, done), waits
-// (bounded) for its other copy and returns.
+// stage stores straight to global memory. Every wait on an mbarrier is bounded
+// and taken by one thread, which publishes the outcome to the whole CTA through
+// shared memory before a barrier, so all threads leave together. Past the limit
+// (PassArgs::tma_wait, in SM clock cycles; 0 -> about 2 s) the kernel marks the
+// solver state (MBS_ETIMEOUT, done), waits with the full bound for the copies it
+// still has in flight (this tile's and the next one's), so no copy writes the
+// shared memory of a CTA that has left, and returns.
 #pragma once
 #include <cuda.h>
 
@@ -36,11 +40,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase of the given parity.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounds below this poll with the non-blocking test_wait: try_wait may suspend
+// the thread for a hardware-chosen time, which could outlast a short bound.
+constexpr long long kTmaPollBelow = 100000;
+// Wait for the phase of the given parity, giving up after `limit` SM clock cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit) {
   const long long t0 = clock64();
+  if (limit < kTmaPollBelow) {
+    while (!mbar_test_wait(bar, parity))
+      if (clock64() - t0 > limit) return false;
+    return true;
+  }
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kTmaWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -90,12 +111,13 @@ __device__ __forceinline__ void tma_fail(const PassArgs& a) {
 // transforms one tile that sits in buf ([N][32]).
 template <int N, int AXIS, class Body>
 __device__ __forceinline__ void tma_tiles(const PassArgs& a, const CUtensorMap* tm, float2* dyn, uint64_t* bar,
-                                          Body body) {
+                                          int* ok, Body body) {
   const int tid = threadIdx.x;
   const int gx = (int)((a.g.N2 + 31) / 32);
   const int ny = (int)(AXIS == 1 ? a.g.N0 : a.g.N1);
   const int ntiles = gx * ny * a.nsub;
   constexpr unsigned kBytes = N * 32 * sizeof(float2);
+  const long long limit = a.tma_wait > 0 ? a.tma_wait : kTmaWaitCycles;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -107,14 +129,19 @@ __device__ __forceinline__ void tma_tiles(const PassArgs& a, const CUtensorMap* 
   for (int k = 0; t < ntiles; k++, t += gridDim.x) {
     const int b = k & 1;
     const int tn = t + gridDim.x;
-    if (tn < ntiles && tid == 0) tma_issue<AXIS>(a, tm, tma_tile(tn, gx, ny), dyn + (b ^ 1) * N * 32, &bar[b ^ 1], kBytes);
-    if (!mbar_wait(&bar[b], (k >> 1) & 1)) {
-      if (tid == 0) {
+    if (tid == 0) {
+      if (tn < ntiles) tma_issue<AXIS>(a, tm, tma_tile(tn, gx, ny), dyn + (b ^ 1) * N * 32, &bar[b ^ 1], kBytes);
+      const bool got = mbar_wait(&bar[b], (k >> 1) & 1, limit);
+      if (!got) {
         tma_fail(a);
-        if (tn < ntiles) mbar_wait(&bar[b ^ 1], ((k + 1) >> 1) & 1);
+        // drain with the full bound: no copy may land after the CTA has left
+        mbar_wait(&bar[b], (k >> 1) & 1, kTmaWaitCycles);
+        if (tn < ntiles) mbar_wait(&bar[b ^ 1], ((k + 1) >> 1) & 1, kTmaWaitCycles);
       }
-      return;
+      *ok = got ? 1 : 0;
     }
+    __syncthreads();  // every thread sees the same outcome of the wait
+    if (!*ok) return;
     body(reinterpret_cast<float2(*)[32]>(dyn + b * N * 32), tma_tile(t, gx, ny));
     fence_proxy_async();  // this tile's generic-proxy accesses before the buffer's next copy
     __syncthreads();
@@ -136,10 +163,11 @@ __global__ void __launch_bounds__(32 * warps_for(N), tma_min_blocks(N)) k_stride
   constexpr int W = warps_for(N);
   extern __shared__ __align__(1024) float2 dyn[];
   __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int ok;
   if (a.state && a.state->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float2* K = a.K;
-  tma_tiles<N, AXIS>(a, &tm, dyn, bar, [&](float2 (*sm)[32], const TmaTile& tl) {
+  tma_tiles<N, AXIS>(a, &tm, dyn, bar, &ok, [&](float2 (*sm)[32], const TmaTile& tl) {
     const int j = a.subs[tl.js];
     const long long i2 = (long long)tl.ib * 32 + lane;
     const bool valid = i2 < a.g.N2;

@@ -118,6 +118,7 @@ def test_host_only_entry_points(lib):
     lib.mbs_default_options(C.byref(opts))
     assert opts.truncation == 8 and opts.alpha == 0.75 and opts.absorb_kappa == 0.5
     assert opts.flags == 0 and opts.periodic_mask == 0 and not opts.split_sizes
+    assert opts.tma_wait_cycles == 0
     lib.mbs_kernel_kind_name.restype = C.c_char_p
     names = [lib.mbs_kernel_kind_name(k).decode() for k in range(pkg.KERNEL_KINDS)]
     assert names == ["corr_x", "rows_first", "strided_fwd", "mid_axis0", "strided_inv", "rows_last", "corr_e",

@@ -1,5 +1,6 @@
 """Batches of independent solves: one graph over several plans gives exactly the
-iterates and iteration counts of the plans run one by one."""
+iterates and iteration counts of the plans run one by one, and each batched solve
+matches the FP64 oracle on its own grid at equal iteration counts."""
 import numpy as np
 import pytest
 
@@ -7,6 +8,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+from oracle import Problem, relative_l2  # noqa: E402
 from synth import frequency_batch  # noqa: E402
 
 
@@ -72,4 +74,27 @@ def test_batch_solves_each_to_its_own_tolerance(problems):
     assert torch.allclose(x, 2 * x1, rtol=1e-5, atol=1e-9)
     b.close()
     for p in batched + single:
+        p.close()
+
+
+@pytest.mark.parametrize("form", ["x", "residual", "tf32"])
+def test_batched_solves_match_the_oracle(problems, form):
+    """Every solve of the batch (uneven grids, explicit uneven subdomain sizes)
+    against the oracle at 30 iterations (3 replays of a graph of 10)."""
+    import paper_2410_02395_gb300 as pkg
+
+    kw = {"residual_form": form == "residual", "corr_tf32": form == "tf32"}
+    batched = _plans(problems, **kw)
+    b = pkg.Batch(batched, graph_iters=10)
+    res = b.iterate(30, 0.0, no_poll=True)
+    for (params, n, src), p, r in zip(problems, batched, res):
+        assert r[1] == 30
+        ref = Problem(n, params["pixel"], params["wavelength"], widths=params["widths"], split=params["split"],
+                      periodic=params["periodic"], t=params["t"], split_sizes_=params["split_sizes"])
+        xr, itr, histr = ref.solve(src, tol=0.0, max_iter=30)
+        x = p.field(like=torch.zeros(1, device="cuda")).cpu().numpy()
+        assert relative_l2(x, xr) < 1e-4, (params["shape"], relative_l2(x, xr))
+        np.testing.assert_allclose(p.history(30), histr, rtol=1e-4, atol=1e-6)
+    b.close()
+    for p in batched:
         p.close()

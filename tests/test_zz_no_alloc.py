@@ -4,7 +4,10 @@ mbs_apply_edge_corrections_noalloc serves callers that must not trigger a
 device allocation when they call (their device memory belongs to another
 allocator or a fixed budget). It computes the same E x as
 mbs_apply_operator(MBS_OP_E) with its scratch in a fixed array inside the
-library; this checks the two agree on two calls in a row, through the C ABI.
+library. These tests call it through the C ABI, twice in a row per plan, and
+compare it with the FP64 oracle's E and with the existing operator entry point;
+the second call must leave the device's free memory unchanged. The scratch keeps
+what the last call left in it, so plans of different shapes follow one another.
 """
 import ctypes as C
 
@@ -15,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-from oracle import relative_l2  # noqa: E402
+from oracle import Problem, relative_l2  # noqa: E402
 from synth import random_field, spheres_medium  # noqa: E402
 
 OP_TOL = 2e-6  # the single-operator tolerance of the parity tests
@@ -32,24 +35,52 @@ def _entry():
     return pkg, lib, f
 
 
-@pytest.mark.parametrize("shape,split,t,tf32", [((48, 40, 36), (2, 2, 2), 4, False),
-                                               ((64, 64, 64), (2, 1, 2), 8, True),
-                                               ((45, 32, 40), (3, 2, 1), 5, False)])
-def test_noalloc_matches_operator_on_two_calls(shape, split, t, tf32):
-    pkg, lib, f = _entry()
+CASES = [((48, 40, 36), (2, 2, 2), 4, False, (False, False, False)),
+         ((64, 64, 64), (2, 1, 2), 8, True, (False, False, False)),
+         ((45, 32, 40), (3, 2, 1), 5, False, (False, False, False)),
+         # axis 1 periodic and unsplit (a_1 = 0: no corrections along it), axis 0 split across its seam
+         ((40, 24, 32), (2, 1, 2), 4, False, (True, True, False))]
+
+
+def _check_two_calls(pkg, lib, f, shape, split, t, tf32, periodic, seeds):
     n = spheres_medium(shape, count=3, r_range=(2, 5), n_range=(1.1, 1.4), seed=21)
-    plan = pkg.Plan(shape, 0.25, 1.0, torch.from_numpy(n).cuda(), boundary_widths=((2, 2),) * 3, split=split,
-                    truncation=t, corr_tf32=tf32)
-    for call, seed in enumerate((31, 32)):
-        x = torch.from_numpy(random_field(shape, seed=seed)).cuda()
+    widths = ((2, 2),) * 3
+    plan = pkg.Plan(shape, 0.25, 1.0, torch.from_numpy(n).cuda(), boundary_widths=widths, split=split,
+                    truncation=t, corr_tf32=tf32, periodic=periodic)
+    ref = Problem(n, 0.25, 1.0, widths=widths, split=split, periodic=periodic, t=t)
+    for call, seed in enumerate(seeds):
+        xh = random_field(shape, seed=seed)
+        x = torch.from_numpy(xh).cuda()
         out = torch.full(shape, complex(7.0, -3.0), dtype=torch.complex64, device="cuda")  # stale output
-        st = f(plan.handle, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()))
-        assert st == 0, lib.mbs_noalloc_last_error().decode()
-        ref = plan.apply("E", x)
         torch.cuda.synchronize()
-        err = relative_l2(out.cpu().numpy(), ref.cpu().numpy())
-        assert err < OP_TOL, (call, err)
+        free0, _ = torch.cuda.mem_get_info()
+        st = f(plan.handle, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()))
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert st == 0, lib.mbs_noalloc_last_error().decode()
+        if call > 0:
+            assert free1 == free0, (free0, free1)
+        got = out.cpu().numpy()
+        want = ref.apply_E(xh.astype(np.complex128))
+        assert relative_l2(got, want) < OP_TOL, (call, relative_l2(got, want))
+        op = plan.apply("E", x)
+        torch.cuda.synchronize()
+        assert relative_l2(got, op.cpu().numpy()) < OP_TOL
     plan.close()
+
+
+@pytest.mark.parametrize("shape,split,t,tf32,periodic", CASES)
+def test_noalloc_matches_oracle_on_two_calls(shape, split, t, tf32, periodic):
+    pkg, lib, f = _entry()
+    _check_two_calls(pkg, lib, f, shape, split, t, tf32, periodic, (31, 32))
+
+
+def test_noalloc_after_a_plan_of_another_shape():
+    """A large plan's call fills much of the scratch; a smaller plan of another
+    shape and split then reads none of what it left."""
+    pkg, lib, f = _entry()
+    _check_two_calls(pkg, lib, f, (96, 80, 64), (3, 2, 2), 6, False, (False,) * 3, (51, 52))
+    _check_two_calls(pkg, lib, f, (20, 36, 28), (1, 3, 2), 3, False, (True, False, False), (53, 54))
 
 
 def test_noalloc_rejects_oversized_grid_and_host_pointers():
