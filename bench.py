@@ -1,20 +1,27 @@
 #!/usr/bin/env python3
 """Benchmark of the MBS hot path: voxel-iterations per second on one GB300.
 
-Workload (default): the domain-decomposed MBS problem on a 256^3 grid at
-lambda/4, split 2x2x2 into 128^3 subdomains with t = 8 edge corrections, 40
-seeded random spheres (radius 4-20 px, n in [1.0, 1.6]) in n = 1.0, 8-px
-absorbing layers, point source at the centre. One step = one iteration of
-Eq. wavesim_iter over the whole grid (all subdomains).
+Workload (default, C5): the domain-decomposed MBS problem at the paper's
+320^3-wavelength scale, a 1280^3 grid at lambda/4 split 4x4x4 into 320^3
+subdomains with t = 8 edge corrections, seeded random spheres (radius 5-40 px,
+n in [1.0, 1.5]) added until 30 % of the volume is filled, 8-px absorbing
+layers, point source at the centre. One step = one iteration of
+Eq. wavesim_iter over the whole grid (all 64 subdomains).
 
 Printed JSON line (one, from rank 0):
-  value       voxel-iterations/s with every buffer resident in HBM, timed with
-              CUDA events on the plan's stream over K graph-replayed iterations
-  e2e         the same metric through the C ABI call mbs_solve with pinned host
-              source/output buffers, host<->device copies inside the timed region
-  roofline    the dominant kernel's algorithmic bytes per launch / its average
-              CUDA-event duration, against the measured HBM copy bandwidth
-  cpu_baseline the FP64 oracle timed on the host cores on a bounded sample
+  value        voxel-iterations/s with every buffer resident in HBM, timed with
+               CUDA events on the plan's stream over K graph-replayed iterations
+               (FP32 edge corrections on the CUDA cores)
+  mixed        the same with the 3xTF32 tensor-core edge corrections
+  e2e          the same metric through the C ABI call mbs_solve with pinned host
+               source/output buffers, host<->device copies inside the timed region
+  roofline     the dominant kernel's algorithmic bytes per launch / its average
+               CUDA-event duration, against the measured HBM copy bandwidth
+  error        relative L2 distance to the FP64 oracle at equal iteration counts,
+               per form, on the workload's recipe at a size the oracle runs
+  cpu_baseline the FP64 oracle timed on the host cores (all of them, and one
+               thread) on a bounded sample of the workload's recipe
+  workloads    value and mixed value of the other single-grid workloads (C2, C3)
 
 With --gpus N > 1 (under torchrun) every rank runs an independent replica of
 the workload on its own GPU (the path has no data exchange on one GPU);
@@ -35,7 +42,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "C2"
+WORKLOAD = "C5"
 WORKLOAD_TEXT = {
     "C1": "C1: 64^3 grid at lambda/4, one periodic subdomain, 6 spheres, 8-px absorbing layers, point source",
     "C2": "C2: 256^3 grid at lambda/4, 2x2x2 subdomains of 128^3, t=8, 40 spheres, 8-px absorbing layers, point source",
@@ -141,6 +148,9 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:  # the first sample before the timed region
+                time.sleep(0.02)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -187,65 +197,236 @@ def build_problem(name):
     return config_problem(name)
 
 
-def cpu_oracle_sample(iters=3, shape=(128, 128, 128)):
-    """The FP64 oracle on the workload's recipe at a reduced grid (bounded sample)."""
+# Bounded samples of a workload's recipe for the oracle on the host: the recipe
+# on a sub-box with one subdomain of the workload's subdomain edge (wrap-removal
+# corrections on every axis), so that the per-voxel work matches.
+CPU_SAMPLE = {"C5": (320, 320, 320), "C3": (128, 128, 128), "C2": (128, 128, 128), "C2P": (123, 123, 123),
+              "C1": (64, 64, 64)}
+REFERENCE_SAMPLE = (128, 128, 128)  # per step of the reference arm (a few seconds each)
+
+
+def oracle_iterations(workload, shape, iters, warm):
+    """The FP64 oracle as it stands: `warm` untimed then `iters` timed iterations of
+    the workload's recipe on `shape` (one subdomain); returns (seconds, cpu seconds)."""
     import numpy as np
 
     from oracle import Problem
     from synth import config_problem
 
-    params, n, src = config_problem(WORKLOAD, shape=shape)
-    p = Problem(n, params["pixel"], params["wavelength"], widths=params["widths"], split=params["split"],
-                periodic=params["periodic"], t=params["t"])
+    params, n, src = config_problem(workload, shape=shape)
+    periodic = params["periodic"]
+    p = Problem(n, params["pixel"], params["wavelength"], widths=params["widths"], split=(1, 1, 1),
+                periodic=periodic, t=params["t"])
     y = p.scaled_source(src)
     x = np.zeros(p.shape, dtype=complex)
-    x, _ = p.iteration(x, y)  # untimed warm-up
-    t0 = time.perf_counter()
+    for _ in range(warm):
+        x, _ = p.iteration(x, y)
+    c0, t0 = time.process_time(), time.perf_counter()
     for _ in range(iters):
         x, _ = p.iteration(x, y)
-    dt = time.perf_counter() - t0
-    vox = float(np.prod(shape))
-    return vox * iters / dt, dt, "C2 recipe (spheres, 8-px layers, point source, split 2x2x2, t=8) on a %s grid " \
-                                 "(subdomains %s), %d iterations after 1 warm-up, %.1f s" % (
-                                     "x".join(map(str, shape)), "x".join(str(s // 2) for s in shape), iters, dt)
+    return time.perf_counter() - t0, time.process_time() - c0
+
+
+def cpu_child(args):
+    """Entry of the child process that times the oracle (its thread count is set
+    in its environment before numpy loads): prints one JSON line."""
+    shape = tuple(int(v) for v in args.cpu_shape.split("x"))
+    dt, cpu = oracle_iterations(args.workload, shape, args.cpu_iters, 0)
+    vox = float(shape[0] * shape[1] * shape[2])
+    print(json.dumps({"value": vox * args.cpu_iters / dt, "seconds": dt, "cpu_seconds": cpu,
+                      "shape": list(shape), "iters": args.cpu_iters}), flush=True)
+    return 0
+
+
+def run_cpu_child(workload, shape, iters, threads, timeout=900):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = str(threads)
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-child", "--workload", workload,
+           "--cpu-shape", "x".join(map(str, shape)), "--cpu-iters", str(iters)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=timeout)
+    if r.returncode != 0:
+        return {"error": r.stderr[-500:]}
+    return json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+
+
+def cpu_baseline(workload):
+    """The oracle on all host cores and on one thread, on a bounded sample."""
+    shape = CPU_SAMPLE.get(workload, (128, 128, 128))
+    ncores = os.cpu_count() or 1
+    allc = run_cpu_child(workload, shape, 1, ncores)
+    one = run_cpu_child(workload, shape, 1, 1)
+    if "error" in allc:
+        return {"value": None, "unit": UNIT, "cores": ncores, "kind": "oracle", "error": allc["error"]}
+    sample = ("%s recipe on a %s sub-box (one subdomain of the workload's subdomain edge, wrap-removal corrections "
+              "on every axis), 1 MBS iteration of the FP64 numpy oracle, %.1f s" % (
+                  workload, "x".join(map(str, shape)), allc["seconds"]))
+    return {"value": allc["value"], "unit": UNIT, "cores": ncores, "kind": "oracle", "sample": sample,
+            "nproc": ncores, "cpu_utilisation": allc["cpu_seconds"] / allc["seconds"],
+            "threads_note": "OMP/OPENBLAS/MKL thread counts set to nproc; the oracle's FFT is numpy code, so only "
+                            "its small matrix products can use more than one core",
+            "single_thread": None if "error" in one else {"value": one["value"], "unit": UNIT, "cores": 1,
+                                                          "seconds": one["seconds"]}}
 
 
 def run_reference(args):
-    """The oracle as it stands, timed on the host cores (rank 0 only)."""
+    """The oracle as it stands, timed on the host cores (rank 0 only): each step
+    one MBS iteration of the workload's recipe on a 128^3 sub-box."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     import numpy as np
 
     from oracle import Problem
     from synth import config_problem
 
-    shape = (128, 128, 128)
-    params, n, src = config_problem(WORKLOAD, shape=shape)
-    p = Problem(n, params["pixel"], params["wavelength"], widths=params["widths"], split=params["split"],
+    shape = REFERENCE_SAMPLE
+    params, n, src = config_problem(args.workload, shape=shape)
+    p = Problem(n, params["pixel"], params["wavelength"], widths=params["widths"], split=(1, 1, 1),
                 periodic=params["periodic"], t=params["t"])
     y = p.scaled_source(src)
     x = np.zeros(p.shape, dtype=complex)
     for _ in range(args.warmup):
         x, _ = p.iteration(x, y)
-    t0 = time.perf_counter()
+    c0, t0 = time.process_time(), time.perf_counter()
     for _ in range(args.steps):
         x, _ = p.iteration(x, y)
     dt = time.perf_counter() - t0
+    cpu = time.process_time() - c0
     vox = float(np.prod(shape))
     v = vox * args.steps / dt
-    sample = ("one MBS iteration per step of the %s workload recipe on a 128^3 grid (split 2x2x2, t=8), "
-              "FP64 numpy oracle, single thread" % WORKLOAD)
+    ncores = os.cpu_count() or 1
+    sample = ("one MBS iteration per step of the %s workload recipe on a %s sub-box (one subdomain, wrap-removal "
+              "corrections on every axis), FP64 numpy oracle with numpy's default threading (%d host cores, "
+              "CPU utilisation %.2f)" % (args.workload, "x".join(map(str, shape)), ncores, cpu / dt))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": "C2 recipe at 128^3 (bounded CPU sample of the 256^3 C2 workload)",
-                       "grid": list(shape), "split": [2, 2, 2], "t": 8},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD_TEXT[args.workload] + " (bounded CPU sample: %s sub-box)"
+                       % "x".join(map(str, shape)), "grid": list(shape), "split": [1, 1, 1], "t": params["t"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": ncores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def timed_iterations(plan, K, warmup, stream, dev, ws, torch, clocks=None):
+    """CUDA-event milliseconds of K iterations (graph replays, no polling) after warm-up,
+    max over ranks."""
+    plan.iterate(max(warmup, 3), 0.0, no_poll=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    if clocks is not None:
+        clocks.start()
+    ev0.record(stream)
+    plan.iterate(K, 0.0, no_poll=True)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop() if clocks is not None else None
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    return ms, clk
+
+
+def error_vs_oracle(pkg, torch, dev, workload, shape=(96, 96, 96), iters=10):
+    """Relative L2 distance (unsquared, and the paper's squared metric) of each form
+    to the FP64 oracle at equal iteration counts, on the workload's recipe and
+    split at a size the oracle runs in seconds."""
+    from oracle import Problem, relative_l2
+    from synth import config_problem
+
+    params, n, src = config_problem(workload, shape=shape)
+    kw = dict(widths=params["widths"], split=params["split"], periodic=params["periodic"], t=params["t"])
+    ref = Problem(n, params["pixel"], params["wavelength"], **kw)
+    xr, _, _ = ref.solve(src, tol=0.0, max_iter=iters)
+    out = {"workload": "%s recipe on %s, split %s, %d iterations" % (
+        workload, "x".join(map(str, shape)), "x".join(map(str, params["split"])), iters)}
+    forms = {"fp32": {}, "mixed_3xtf32": {"corr_tf32": True}, "residual_form": {"residual_form": True},
+             "plain_steps": {"plain_steps": True}}
+    for name, fkw in forms.items():
+        plan = pkg.Plan(shape, params["pixel"], params["wavelength"], torch.from_numpy(n).to(dev),
+                        boundary_widths=params["widths"], split=params["split"], truncation=params["t"],
+                        periodic=params["periodic"], **fkw)
+        x, it, _ = plan.solve(torch.from_numpy(src).to(dev), tol=0.0, max_iter=iters)
+        e = relative_l2(x.cpu().numpy(), xr)
+        out[name] = {"rel_l2": e, "rel_l2_squared": e * e, "iterations": it}
+        plan.close()
+    return out
+
+
+def cufft_comparison(torch, dev, info, prof, K, reps=5):
+    """The vendor FFT (cuFFT through torch.fft) on the same subdomains, timed here
+    only for comparison (the library never calls it): batched 3-D C2C forward
+    transform, pointwise propagator-like multiply, inverse transform, against the
+    CUDA-event time of the library's five transform passes of one iteration (which
+    also carry the fused medium, source, correction and update work)."""
+    sizes = info["sizes"]
+    if any(len(set(s)) != 1 for s in sizes):
+        return None  # uneven subdomains: no single batched transform
+    nsub = len(sizes[0]) * len(sizes[1]) * len(sizes[2])
+    shp = (nsub, sizes[0][0], sizes[1][0], sizes[2][0])
+    g = torch.Generator(device=dev).manual_seed(7)
+    a = torch.complex(torch.randn(shp, generator=g, device=dev), torch.randn(shp, generator=g, device=dev))
+    mul = torch.complex(torch.rand(shp[1:], generator=g, device=dev), torch.rand(shp[1:], generator=g, device=dev))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    fwd = inv = both = 0.0
+    for r in range(reps + 2):
+        ev[0].record()
+        b = torch.fft.fftn(a, dim=(1, 2, 3))
+        ev[1].record()
+        b.mul_(mul)
+        ev[2].record()
+        c = torch.fft.ifftn(b, dim=(1, 2, 3))
+        ev[3].record()
+        torch.cuda.synchronize(dev)
+        del b, c
+        if r >= 2:
+            fwd += ev[0].elapsed_time(ev[1]) / reps
+            inv += ev[2].elapsed_time(ev[3]) / reps
+            both += ev[0].elapsed_time(ev[3]) / reps
+    del a, mul
+    torch.cuda.empty_cache()
+    ours = sum(prof[k][1] for k in ("rows_first", "strided_fwd", "mid_axis0", "strided_inv", "rows_last")) / K
+    return {"batch": list(shp), "cufft_fwd_ms": fwd, "cufft_inv_ms": inv, "cufft_fwd_mul_inv_ms": both,
+            "library_transform_passes_ms": ours,
+            "ratio_library_over_cufft": ours / both if both > 0 else None,
+            "how": "torch.fft.fftn / ifftn (cuFFT) on a contiguous batch of the subdomains, out of place, CUDA "
+                   "events, %d repetitions after 2; the library's passes read and write the subdomains inside the "
+                   "global grid and fuse the medium, source, corrections and update" % reps}
+
+
+def workload_values(pkg, torch, dev, names, steps, warmup, ws):
+    """Device-timed value (and the mixed form's) of other single-grid workloads."""
+    import numpy as np
+
+    out = {}
+    for name in names:
+        params, n, src = build_problem(name)
+        shape = params["shape"]
+        vox = int(np.prod(shape))
+        stream = torch.cuda.Stream(device=dev)
+        n_dev = torch.from_numpy(n).to(dev)
+        src_dev = torch.from_numpy(src).to(dev)
+        rec = {"workload": WORKLOAD_TEXT[name]}
+        for form, fkw in (("value", {}), ("mixed", {"corr_tf32": True})):
+            with torch.cuda.stream(stream):
+                p = pkg.Plan(shape, params["pixel"], params["wavelength"], n_dev, boundary_widths=params["widths"],
+                             split=params["split"], truncation=params["t"], periodic=params["periodic"],
+                             stream=stream.cuda_stream, **fkw)
+                G = p.info()["graph_iters"]
+                K = max(G, (max(steps, 100) // G) * G)
+                p.set_source(src_dev)
+                ms, _ = timed_iterations(p, K, warmup, stream, dev, ws, torch)
+                p.close()
+            rec[form] = whole_job_rate(vox * K, ws, ms / 1e3)
+            rec[form + "_ms_per_step"] = ms / K
+        out[name] = rec
+        del n_dev, src_dev
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_batch(args, pkg, torch, ws, rank, dev):
@@ -330,21 +511,29 @@ def run_batch(args, pkg, torch, ws, rank, dev):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--e2e-iters", type=int, default=100, help="iterations per mbs_solve call in the e2e leg")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-iters", type=int, default=20, help="iterations per mbs_solve call in the e2e leg")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance leg")
+    ap.add_argument("--no-error", action="store_true", help="skip the error-vs-oracle leg")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other single-grid workloads (C2, C3)")
+    ap.add_argument("--ttt", action="store_true", help="run the time-to-tolerance leg (long at 1280^3)")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance leg of C4")
     ap.add_argument("--ttt-max-iter", type=int, default=40000)
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_TEXT),
-                    help="benchmark workload (default: the C2 configuration)")
+                    help="benchmark workload (default: the 1280^3 configuration C5)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 3xTF32-correction timing")
     ap.add_argument("--t-sweep", default="", help="comma-separated truncation widths: ms per iteration for each "
                     "on the same workload (Sec. 4.2.1, Fig. 7c)")
+    ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-shape", default="128x128x128", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-iters", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_child:
+        return cpu_child(args)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -369,32 +558,19 @@ def main():
     shape = params["shape"]
     vox = int(np.prod(shape))
     stream = torch.cuda.Stream(device=dev)
+    n_dev = torch.from_numpy(n).to(dev)
+    src_dev = torch.from_numpy(src).to(dev)
+    kw = dict(boundary_widths=params["widths"], split=params["split"], truncation=params["t"],
+              periodic=params["periodic"], stream=stream.cuda_stream)
     with torch.cuda.stream(stream):
-        plan = pkg.Plan(shape, params["pixel"], params["wavelength"], torch.from_numpy(n).to(dev),
-                        boundary_widths=params["widths"], split=params["split"], truncation=params["t"],
-                        periodic=params["periodic"], stream=stream.cuda_stream)
+        plan = pkg.Plan(shape, params["pixel"], params["wavelength"], n_dev, **kw)
         info = plan.info()
         G = info["graph_iters"]
         K = max(G, (args.steps // G) * G)  # whole graph replays
-        src_dev = torch.from_numpy(src).to(dev)
         plan.set_source(src_dev)
-        plan.iterate(max(args.warmup, 3), 0.0, no_poll=True)
 
         # ---- device-resident timed region -------------------------------------
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        clocks = ClockSampler(dev.index)
-        if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize(dev)
-        clocks.start()
-        ev0.record(stream)
-        status, iters_done, eps = plan.iterate(K, 0.0, no_poll=True)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-        clk = clocks.stop()
-        ms = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
-        if ws > 1:
-            torch.distributed.barrier()
+        ms, clk = timed_iterations(plan, K, args.warmup, stream, dev, ws, torch, ClockSampler(dev.index))
         value = whole_job_rate(vox * K, ws, ms / 1e3)
 
         # ---- per-kernel CUDA-event timing (same workload, kernels launched one by one)
@@ -407,11 +583,16 @@ def main():
         dom_launches, dom_ms = prof[dom]
         bytes_per_launch = kernel_bytes_per_voxel(dom, fr) * vox / max(1.0, dom_launches / K)
         achieved = bytes_per_launch / (dom_ms / dom_launches / 1e3) / 1e9
+        bytes_iter = sum(kernel_bytes_per_voxel(k, fr) for k in prof) * vox
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": MEASURED_TRAFFIC.get((args.workload, dom)), "kernel": dom, "peak_source": peak_src,
                     "share": prof[dom][1] / tot if tot else None,
                     "bytes_per_launch": bytes_per_launch,
+                    "iteration": {"bytes_per_voxel": bytes_iter / vox,
+                                  "GBps_graph_replayed": bytes_iter / (ms / K / 1e3) / 1e9,
+                                  "frac_graph_replayed": bytes_iter / (ms / K / 1e3) / 1e9 / peak},
                     "kernels": {k: {"launches": v[0], "ms_per_iter": v[1] / K,
+                                    "bytes_per_voxel": kernel_bytes_per_voxel(k, fr),
                                     "GBps": (kernel_bytes_per_voxel(k, fr) * vox * K / (v[1] / 1e3) / 1e9)
                                     if v[1] > 0 else None} for k, v in prof.items()}}
 
@@ -432,51 +613,42 @@ def main():
                    "h2d_bytes_per_step": vox * 8, "d2h_bytes_per_step": vox * 8 + 8 * args.e2e_iters,
                    "step": "one mbs_solve call: pinned host source -> device, %d iterations, field -> pinned host"
                            % args.e2e_iters}
-
+            del hsrc, hout
         plan.close()
-        n_dev = torch.from_numpy(n).to(dev)
-        kw = dict(boundary_widths=params["widths"], split=params["split"], truncation=params["t"],
-                  periodic=params["periodic"], stream=stream.cuda_stream)
 
         # ---- the mixed form: 3xTF32 tensor-core edge corrections ---------------
         mixed = None
         if not args.no_mixed and info["a"] != [0, 0, 0]:
             pm = pkg.Plan(shape, params["pixel"], params["wavelength"], n_dev, corr_tf32=True, **kw)
             pm.set_source(src_dev)
-            pm.iterate(max(args.warmup, 3), 0.0, no_poll=True)
-            if ws > 1:
-                torch.distributed.barrier()
-            torch.cuda.synchronize(dev)
-            ev0.record(stream)
-            pm.iterate(K, 0.0, no_poll=True)
-            ev1.record(stream)
-            torch.cuda.synchronize(dev)
-            msm = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
+            msm, _ = timed_iterations(pm, K, args.warmup, stream, dev, ws, torch)
             pm.close()
             mixed = {"value": whole_job_rate(vox * K, ws, msm / 1e3), "unit": UNIT, "ms_per_step": msm / K,
                      "corrections": "3xTF32 mma.sync m16n8k8, FP32 accumulate"}
 
+        # ---- the plain form: one launch per step, residual and stop test on the host
+        Kp = max(5, K // 4)
+        pp = pkg.Plan(shape, params["pixel"], params["wavelength"], n_dev, plain_steps=True, **kw)
+        pp.set_source(src_dev)
+        msp, _ = timed_iterations(pp, Kp, args.warmup, stream, dev, ws, torch)
+        pp.close()
+        plain = {"value": whole_job_rate(vox * Kp, ws, msp / 1e3), "unit": UNIT, "ms_per_step": msp / Kp,
+                 "steps": Kp, "how": "MBS_FLAG_PLAIN_STEPS: every step of the iteration its own launch (about 16 "
+                                     "per iteration), FP32 corrections on the CUDA cores, no CUDA graph, residual "
+                                     "summed and stop test taken on the host after every iteration"}
+
         # ---- the same iterations launched kernel by kernel from the host -----
-        # (no CUDA graph: one launch per pass and iteration, host launch cost included)
-        Kn = max(10, K // 10)
+        Kn = max(10, K // 2)
         pn = pkg.Plan(shape, params["pixel"], params["wavelength"], n_dev, no_graph=True, **kw)
         pn.set_source(src_dev)
-        pn.iterate(max(args.warmup, 3), 0.0, no_poll=True)
-        if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize(dev)
-        ev0.record(stream)
-        pn.iterate(Kn, 0.0, no_poll=True)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-        msn = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
+        msn, _ = timed_iterations(pn, Kn, args.warmup, stream, dev, ws, torch)
         pn.close()
         no_graph = {"value": whole_job_rate(vox * Kn, ws, msn / 1e3), "unit": UNIT, "ms_per_step": msn / Kn,
                     "steps": Kn, "how": "same kernels, launched one by one from the host (MBS_FLAG_NO_GRAPH)"}
 
         # ---- time to tolerance (residual form: no complex64 floor) -----------
         ttt_line = None
-        if not args.no_ttt:
+        if args.ttt:
             pr = pkg.Plan(shape, params["pixel"], params["wavelength"], n_dev, residual_form=True, **kw)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
@@ -496,20 +668,22 @@ def main():
                 pt = pkg.Plan(shape, params["pixel"], params["wavelength"], n_dev, **kt)
                 pt.set_source(src_dev)
                 Kt = max(10, K // 4)
-                pt.iterate(max(args.warmup, 3), 0.0, no_poll=True)
-                torch.cuda.synchronize(dev)
-                ev0.record(stream)
-                pt.iterate(Kt, 0.0, no_poll=True)
-                ev1.record(stream)
-                torch.cuda.synchronize(dev)
-                tsweep.append({"t": tv, "ms_per_step": ev0.elapsed_time(ev1) / Kt, "c_abs": abs(pt.info()["c"])})
+                mst, _ = timed_iterations(pt, Kt, args.warmup, stream, dev, ws, torch)
+                tsweep.append({"t": tv, "ms_per_step": mst / Kt, "c_abs": abs(pt.info()["c"])})
                 pt.close()
+    del n_dev, src_dev, n, src
+    torch.cuda.empty_cache()
+    cufft = cufft_comparison(torch, dev, info, prof, K)
 
+    error = None
+    if rank == 0 and not args.no_error:
+        error = error_vs_oracle(pkg, torch, dev, args.workload)
+    extra = None
+    if not args.no_extra and args.workload == "C5":
+        extra = workload_values(pkg, torch, dev, ["C2", "C3"], args.steps, args.warmup, ws)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        os.environ.setdefault("OMP_NUM_THREADS", "1")
-        v, dt, sample = cpu_oracle_sample()
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = cpu_baseline(args.workload)
 
     if rank == 0:
         line = {
@@ -530,7 +704,11 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "mixed": mixed,
+            "plain": plain,
+            "cufft": cufft,
             "no_graph": no_graph,
+            "error": error,
+            "workloads": extra,
             "time_to_tol": ttt_line,
         }
         if args.t_sweep:

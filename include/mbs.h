@@ -20,7 +20,10 @@
  *    each pointer (cudaPointerGetAttributes) and copies host data through the
  *    plan's stream. Host copies are counted in the timing of the call.
  *  - Every call is synchronous with respect to the host unless stated, and all
- *    device work runs on the plan's stream.
+ *    device work runs on the plan's stream. Device inputs are read on that
+ *    stream: work on them queued on other streams must be complete (or ordered
+ *    before it) when the call is made.
+ *    (The Python binding synchronises torch's current stream before each call.)
  *  - Errors are returned as mbs_status; nothing is thrown or aborted across the
  *    ABI. mbs_last_error() returns a thread-local description of the last error.
  *  - Ownership: the caller owns every array passed in; the plan copies what it
@@ -99,6 +102,14 @@ typedef enum mbs_operator {
 #define MBS_FLAG_FORCE_TMA (1u << 4) /* keep every tensor-map feed the plan can build instead of timing
                                      the TMA-fed against the register-fed axis-1 pass at plan
                                      creation and keeping the faster (results are identical)      */
+#define MBS_FLAG_PLAIN_STEPS (1u << 5) /* comparison form of the iteration: every step of
+                                     Eq. wavesim_iter is its own launch over the whole grid (E x,
+                                     u = B x + y - E x, three forward FFT passes, the propagator,
+                                     three inverse passes, d = x - w, E d, r = B d - E d, |r|^2,
+                                     the update), no fused prologues or epilogues, no CUDA graph,
+                                     and the residual summed and the stop test taken on the host
+                                     after every iteration. Same iterates as the default form up to
+                                     FP32 rounding; not with MBS_FLAG_RESIDUAL_FORM or in batches. */
 
 typedef struct mbs_options {
   int32_t truncation;        /* t, the kept edge width (Sec. 3, Fig. 5); 0 -> 8 (Sec. 3.3)      */
@@ -181,6 +192,17 @@ MBS_API mbs_status mbs_apply_operator(mbs_plan *plan, int32_t which, const void 
  * y = -c S (Eq. LV); only the bounding box of S's non-zeros is read per step.
  */
 MBS_API mbs_status mbs_set_source(mbs_plan *plan, const void *source);
+
+/*
+ * Warm start (resume): after mbs_set_source, replace the field x = 0 by x0
+ * (complex64, shape; host or device) and restart the iteration count and the
+ * history. The iteration converges from any start (Sec. 3.1); eps_n stays
+ * normalised by ||Gamma^-1 y||, the residual of x = 0, so a solve resumed from
+ * its last field continues with the same eps (eps_0 < 1 for a good x0).
+ * Uses (and on first use allocates) the plan's staging buffers. Errors:
+ * MBS_EINVAL without a source.
+ */
+MBS_API mbs_status mbs_set_initial_field(mbs_plan *plan, const void *x0);
 
 /*
  * Run up to n_iter iterations of Eq. wavesim_iter from the current state,

@@ -76,6 +76,7 @@ def load_library(path=None):
     lib.mbs_plan_get_info.argtypes = [vp, C.POINTER(_Info)]
     lib.mbs_apply_operator.argtypes = [vp, i32, vp, vp]
     lib.mbs_set_source.argtypes = [vp, vp]
+    lib.mbs_set_initial_field.argtypes = [vp, vp]
     lib.mbs_iterate.argtypes = [vp, i32, dbl, i32, C.POINTER(i32), C.POINTER(dbl)]
     lib.mbs_get_field.argtypes = [vp, vp]
     lib.mbs_get_history.argtypes = [vp, C.POINTER(dbl), i32, C.POINTER(i32)]
@@ -92,7 +93,7 @@ def load_library(path=None):
     lib.mbs_last_error.argtypes = []
     lib.mbs_last_error.restype = C.c_char_p
     for name in ("mbs_plan_create", "mbs_workspace_bytes", "mbs_plan_get_info", "mbs_apply_operator",
-                 "mbs_set_source", "mbs_iterate", "mbs_get_field", "mbs_get_history", "mbs_solve",
+                 "mbs_set_source", "mbs_set_initial_field", "mbs_iterate", "mbs_get_field", "mbs_get_history", "mbs_solve",
                  "mbs_profile_iterations", "mbs_batch_create", "mbs_batch_iterate"):
         getattr(lib, name).restype = C.c_int
     if path is None:
@@ -107,7 +108,12 @@ def _check(lib, status, ok=(0,)):
 
 
 class _Buf:
-    """A pointer to complex64 C-ordered data, keeping its owner alive."""
+    """A pointer to complex64 C-ordered data, keeping its owner alive.
+
+    The library reads and writes device data on the plan's own stream. For a CUDA
+    tensor, torch's current stream on its device is synchronised first, so that
+    work torch has queued on that tensor (its initialisation, say) is complete
+    before the library's stream reads it."""
 
     def __init__(self, arr, shape, writable=False):
         self.owner = None
@@ -127,6 +133,8 @@ class _Buf:
                 if writable:
                     raise ValueError("output tensor must be contiguous")
                 arr = arr.contiguous()
+            if arr.is_cuda:
+                torch.cuda.current_stream(arr.device).synchronize()
             self.owner = arr
             self.ptr = arr.data_ptr()
             return
@@ -153,7 +161,7 @@ class Plan:
     def __init__(self, shape, pixel_size, wavelength, refractive_index, boundary_widths=((0, 0),) * 3,
                  split=(1, 1, 1), truncation=8, alpha=0.75, periodic=(False, False, False), kappa=0.5,
                  split_sizes=None, graph_iters=0, no_graph=False, corr_tf32=False, residual_form=False,
-                 no_tma=False, force_tma=False, tma_wait_cycles=0, stream=None, workspace=None):
+                 no_tma=False, force_tma=False, plain_steps=False, tma_wait_cycles=0, stream=None, workspace=None):
         self.lib = load_library()
         self.shape = tuple(int(s) for s in shape)
         opts = _Options()
@@ -164,7 +172,7 @@ class Plan:
         opts.absorb_kappa = float(kappa)
         opts.graph_iters = int(graph_iters)
         opts.flags = (1 if no_graph else 0) | (2 if corr_tf32 else 0) | (4 if residual_form else 0) | \
-            (8 if no_tma else 0) | (16 if force_tma else 0)
+            (8 if no_tma else 0) | (16 if force_tma else 0) | (32 if plain_steps else 0)
         opts.tma_wait_cycles = int(tma_wait_cycles)
         self._split_sizes = None
         if split_sizes is not None:
@@ -240,6 +248,11 @@ class Plan:
     def set_source(self, source):
         sb = _Buf(source, self.shape)
         _check(self.lib, self.lib.mbs_set_source(self.handle, C.c_void_p(sb.ptr)))
+
+    def set_initial_field(self, x0):
+        """Warm start from x0 after set_source (eps stays normalised by the residual of x = 0)."""
+        xb = _Buf(x0, self.shape)
+        _check(self.lib, self.lib.mbs_set_initial_field(self.handle, C.c_void_p(xb.ptr)))
 
     def iterate(self, n_iter, tol=0.0, no_poll=False):
         """Run up to n_iter iterations; returns (status_name, iterations, residual)."""

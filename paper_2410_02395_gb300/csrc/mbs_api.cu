@@ -149,7 +149,7 @@ struct mbs_plan {
   DevState* free_state;  // never marked done (operator applications)
   double* history;
   int* box_dev;
-  double* host_pinned;  // 64 doubles
+  double* host_pinned;  // plain form: kPlainBlocks partial sums read back every iteration
   DevState* host_state;
   GridDesc g;
   AxisTables tb;
@@ -291,6 +291,8 @@ mbs_status validate_and_fill(mbs_plan* p, const int64_t shape[3], double h, doub
   p->flags = o ? o->flags : 0u;
   p->graph_iters = (o && o->graph_iters > 0) ? o->graph_iters : 0;
   if (o && o->tma_wait_cycles < 0) return fail(MBS_EINVAL, "tma_wait_cycles must be >= 0");
+  if ((p->flags & MBS_FLAG_PLAIN_STEPS) && (p->flags & MBS_FLAG_RESIDUAL_FORM))
+    return fail(MBS_EINVAL, "the plain-step form has no residual form");
   p->tma_wait = o ? (long long)o->tma_wait_cycles : 0;
   int k = 0;
   for (int d = 0; d < 3; d++) {
@@ -847,6 +849,125 @@ cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
   return cudaSuccess;
 }
 
+// One iteration in the plain form (MBS_FLAG_PLAIN_STEPS): one launch per step,
+// the residual's block partials left in p->partials for the host.
+cudaError_t enqueue_iteration_plain(mbs_plan* p) {
+  cudaError_t e = cudaSuccess;
+  PlainArgs q;
+  memset(&q, 0, sizeof(q));
+  q.K = p->K;
+  q.X = p->x;
+  q.B = p->B;
+  q.C = p->ebuf;
+  if (p->have_source) {
+    q.S = p->src;
+    for (int i = 0; i < 6; i++) q.sbox[i] = p->sbox[i];
+  }
+  q.c = make_float2((float)p->c_re, (float)p->c_im);
+  q.mc = make_float2((float)-p->c_re, (float)-p->c_im);
+  const double ck0r = p->c_re * p->k0_re - p->c_im * p->k0_im;
+  const double ck0i = p->c_re * p->k0_im + p->c_im * p->k0_re;
+  q.ck0 = make_float2((float)ck0r, (float)ck0i);
+  q.alpha = (float)p->alpha;
+  q.tb = p->tb;
+  q.g = p->g;
+  q.partials = p->partials;
+  auto step = [&](int mode) {
+    q.mode = mode;
+    return launch_plain_step(q, p->stream);
+  };
+  if (p->has_shell) e = run_corr(p, p->x, p->ebuf, p->state);  // E x, every axis
+  if (!e) e = step(PLAIN_U);
+  PassArgs a = base_args(p);
+  a.X = p->K;
+  a.Xout = p->K;
+  a.state = p->state;
+  if (!e) e = run_transform_chain(p, a, FIRST_PLAIN, MID_FWD, nullptr);  // forward: axis 2, axis 1, axis 0
+  if (!e) e = step(PLAIN_PROP);
+  a.mode = MID_INV;  // inverse: axis 0 (with 1/(n0 n1 n2)), axis 1, axis 2
+  for (auto& gx : p->groups[0]) {
+    if (e) break;
+    a.nsub = gx.nsub;
+    memcpy(a.subs, gx.subs, sizeof(a.subs));
+    set_len_tables(p, a, gx.n);
+    e = launch_mid(gx.n, a, p->stream);
+  }
+  for (auto& gy : p->groups[1]) {
+    if (e || gy.n == 1) continue;
+    a.nsub = gy.nsub;
+    memcpy(a.subs, gy.subs, sizeof(a.subs));
+    set_len_tables(p, a, gy.n);
+    e = strided_pass(p, a, gy.n, true);
+  }
+  if (!e) e = run_rows_last(p, a, LAST_PLAIN, false, nullptr);
+  if (!e) e = step(PLAIN_D);
+  if (!e && p->has_shell) e = run_corr(p, p->K, p->ebuf, p->state);  // E d
+  if (!e) e = step(PLAIN_R);
+  if (!e) e = step(PLAIN_NORM);
+  if (!e) e = step(PLAIN_UPD);
+  return e;
+}
+
+// The iteration loop of the plain form: after every iteration the host reads the
+// residual's partial sums, adds them in FP64 and takes the stop test (the same
+// rule as the device-side state_update), then writes the state and the history
+// back to the device so that mbs_get_history and mbs_get_field work as usual.
+mbs_status iterate_plain(mbs_plan* p, int n_iter, double tol, DevState* out) {
+  if (!p->host_pinned) CU(cudaMallocHost((void**)&p->host_pinned, kPlainBlocks * sizeof(double)));
+  DevState hs;
+  CU(cudaMemcpyAsync(p->host_state, p->state, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  hs = *p->host_state;
+  const int it0 = hs.iter;
+  std::vector<double> hist;
+  for (int i = 0; i < n_iter && !hs.done; i++) {
+    cudaError_t e = enqueue_iteration_plain(p);
+    if (e) return fail(MBS_ECUDA, std::string("plain iteration launch: ") + cudaGetErrorString(e));
+    CU(cudaMemcpyAsync(p->host_pinned, p->partials, kPlainBlocks * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaMemcpyAsync(p->host_state, p->state, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    if (p->host_state->status) {  // a bounded wait expired inside a pass
+      hs.status = p->host_state->status;
+      hs.done = 1;
+      break;
+    }
+    double R = 0.0;
+    for (int b = 0; b < kPlainBlocks; b++) R += p->host_pinned[b];
+    if (hs.iter == 0 && !hs.r0_fixed) hs.R0 = R;
+    const double eps = hs.R0 > 0.0 ? sqrt(R / hs.R0) : 0.0;
+    hist.push_back(eps);
+    hs.eps = eps;
+    hs.iter += 1;
+    if (!isfinite(eps) || !isfinite(R)) {
+      hs.status = MBS_ENAN;
+      hs.done = 1;
+      break;
+    }
+    if (eps < hs.best) {
+      hs.best = eps;
+      hs.rise = 0;
+    } else if (eps > 4.0 * hs.best && eps > 1e-3) {
+      hs.rise += 1;
+    } else {
+      hs.rise = 0;
+    }
+    if (hs.rise >= 20) {
+      hs.status = MBS_EDIVERGE;
+      hs.done = 1;
+    } else if (eps < tol || hs.iter >= hs.max_iter) {
+      hs.done = 1;
+    }
+  }
+  const int nh = std::max(0, std::min((int)hist.size(), kHistCap - it0));
+  if (nh > 0)
+    CU(cudaMemcpyAsync(p->history + it0, hist.data(), nh * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  *p->host_state = hs;
+  CU(cudaMemcpyAsync(p->state, p->host_state, sizeof(DevState), cudaMemcpyHostToDevice, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  *out = hs;
+  return MBS_OK;
+}
+
 mbs_status ensure_graph(mbs_plan* p) {
   if (p->graph_ready) return MBS_OK;
   cudaGraph_t g;
@@ -1213,15 +1334,64 @@ mbs_status mbs_set_source(mbs_plan* p, const void* source) {
   return MBS_OK;
 }
 
+mbs_status mbs_set_initial_field(mbs_plan* p, const void* x0) {
+  g_err.clear();
+  if (!p || !x0) return fail(MBS_EINVAL, "null argument");
+  if (!p->have_source) return fail(MBS_EINVAL, "mbs_set_source must come first");
+  const int64_t nv = nvox(p);
+  // x0 into the staging buffer (the operator below needs x = 0 and its own buffers)
+  if (!p->tmp_in) CU(cudaMalloc((void**)&p->tmp_in, nv * sizeof(float2)));
+  const cudaMemcpyKind kind = is_device_ptr(x0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CU(cudaMemcpyAsync(p->tmp_in, x0, nv * sizeof(float2), kind, p->stream));
+  // ||r_0||^2 of the cold start, ||Gamma^-1 y||^2, normalises eps as for x_0 = 0
+  if (!p->tmp_out) CU(cudaMalloc((void**)&p->tmp_out, nv * sizeof(float2)));
+  CU(launch_zero(p->x, nv, p->stream));
+  mbs_status st = mbs_apply_operator(p, MBS_OP_PRECOND, p->x, p->tmp_out);
+  if (st) return st;
+  if (!p->host_pinned) CU(cudaMallocHost((void**)&p->host_pinned, kPlainBlocks * sizeof(double)));
+  PlainArgs q;
+  memset(&q, 0, sizeof(q));
+  q.K = p->tmp_out;
+  q.tb = p->tb;
+  q.g = p->g;
+  q.partials = p->partials;
+  q.mode = PLAIN_NORM;
+  CU(launch_plain_step(q, p->stream));
+  CU(cudaMemcpyAsync(p->host_pinned, p->partials, kPlainBlocks * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  double R0 = 0.0;
+  for (int b = 0; b < kPlainBlocks; b++) R0 += p->host_pinned[b];
+  CU(cudaMemcpyAsync(p->x, p->tmp_in, nv * sizeof(float2), cudaMemcpyDeviceToDevice, p->stream));
+  if (p->resform) {  // r'_0 = Gamma^-1 (A x_0 - y), x_0 in the high word, low word zero
+    CU(cudaMemsetAsync(p->xlo, 0, nv * sizeof(unsigned), p->stream));
+    st = mbs_apply_operator(p, MBS_OP_PRECOND, p->x, p->r);
+    if (st) return st;
+    CU(launch_negate_copy(p->r, p->r, nv, p->stream));
+  }
+  CU(launch_state_arm(p->state, 0, 0.0, 1, kHistCap, p->stream));
+  CU(cudaMemcpyAsync(p->host_state, p->state, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  p->host_state->R0 = R0;
+  p->host_state->r0_fixed = 1;
+  CU(cudaMemcpyAsync(p->state, p->host_state, sizeof(DevState), cudaMemcpyHostToDevice, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  return MBS_OK;
+}
+
 mbs_status mbs_iterate(mbs_plan* p, int32_t n_iter, double tol, int32_t no_poll, int32_t* iters_done,
                        double* residual) {
   g_err.clear();
   if (!p) return fail(MBS_EINVAL, "null plan");
   if (n_iter < 0) return fail(MBS_EINVAL, "n_iter must be >= 0");
   CU(launch_state_arm(p->state, n_iter, tol, 0, kHistCap, p->stream));
-  const bool use_graph = !(p->flags & MBS_FLAG_NO_GRAPH);
-  int remaining = n_iter;
+  const bool plain = (p->flags & MBS_FLAG_PLAIN_STEPS) != 0;
+  const bool use_graph = !(p->flags & MBS_FLAG_NO_GRAPH) && !plain;
+  int remaining = plain ? 0 : n_iter;
   DevState hs;
+  if (plain) {
+    mbs_status st = iterate_plain(p, n_iter, tol, &hs);
+    if (st) return st;
+  }
   if (use_graph && remaining >= p->graph_iters) {
     mbs_status st = ensure_graph(p);
     if (st) return st;
@@ -1312,6 +1482,7 @@ mbs_status mbs_profile_iterations(mbs_plan* p, int32_t n_iter, int32_t launches[
                                   double ms[MBS_KERNEL_KINDS]) {
   g_err.clear();
   if (!p || n_iter < 0) return fail(MBS_EINVAL, "bad argument");
+  if (p->flags & MBS_FLAG_PLAIN_STEPS) return fail(MBS_EINVAL, "per-kernel profiling is for the fused form");
   for (int k = 0; k < MBS_KERNEL_KINDS; k++) {
     if (launches) launches[k] = 0;
     if (ms) ms[k] = 0.0;
@@ -1402,8 +1573,10 @@ mbs_status mbs_batch_create(mbs_batch** out, int32_t nplans, mbs_plan* const* pl
   g_err.clear();
   if (!out || nplans < 1 || !plans) return fail(MBS_EINVAL, "bad batch arguments");
   *out = nullptr;
-  for (int i = 0; i < nplans; i++)
+  for (int i = 0; i < nplans; i++) {
     if (!plans[i]) return fail(MBS_EINVAL, "null plan in batch");
+    if (plans[i]->flags & MBS_FLAG_PLAIN_STEPS) return fail(MBS_EINVAL, "plain-step plans cannot be batched");
+  }
   mbs_batch* b = new mbs_batch();
   b->plans.assign(plans, plans + nplans);
   b->gen.assign(nplans, ~0u);
@@ -1508,6 +1681,7 @@ void mbs_plan_destroy(mbs_plan* p) {
   if (p->tmp_in) cudaFree(p->tmp_in);
   if (p->tmp_out) cudaFree(p->tmp_out);
   if (p->host_state) cudaFreeHost(p->host_state);
+  if (p->host_pinned) cudaFreeHost(p->host_pinned);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
 }

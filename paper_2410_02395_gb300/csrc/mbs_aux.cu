@@ -261,12 +261,13 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-template <int TP>
+// TC: the truncation width when known at compile time (t == TP == 8), 0 otherwise.
+template <int TP, int TC>
 __global__ void __launch_bounds__(128) k_corr_tc(const __grid_constant__ CorrArgs a) {
   __shared__ float As[4][64][TP + 4];  // per warp; +4 keeps the fragment reads conflict-free
   __shared__ float Wr[TP][TP + 1];     // real W (not scaled by c), zero padded
   if (a.state && a.state->done) return;
-  const int d = a.axis, t = a.g.t;
+  const int d = a.axis, t = TC > 0 ? TC : a.g.t;
   const AxisDesc& ax = a.g.ax[d];
   const long long N0 = a.g.N0, N1 = a.g.N1, N2 = a.g.N2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -373,9 +374,21 @@ __global__ void __launch_bounds__(128) k_corr_tc(const __grid_constant__ CorrArg
   if (!valid) return;
   const float2 c = a.c;
   const long long out0 = base + (long long)(side ? off + n - t : off) * stride;
-  for (int q = 0; q < t; q++) {
-    const float2 v = cmul(c, make_float2(As[warp][2 * lane][q], As[warp][2 * lane + 1][q]));
-    put(a.C, out0 + (long long)q * stride, v, add);
+  if constexpr (TC > 0) {
+    // every load of the outputs the earlier axes wrote is issued before any store
+    float2 prev[TC];
+#pragma unroll
+    for (int q = 0; q < TC; q++) prev[q] = add ? a.C[out0 + (long long)q * stride] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < TC; q++) {
+      const float2 v = cmul(c, make_float2(As[warp][2 * lane][q], As[warp][2 * lane + 1][q]));
+      a.C[out0 + (long long)q * stride] = cadd(prev[q], v);
+    }
+  } else {
+    for (int q = 0; q < t; q++) {
+      const float2 v = cmul(c, make_float2(As[warp][2 * lane][q], As[warp][2 * lane + 1][q]));
+      put(a.C, out0 + (long long)q * stride, v, add);
+    }
   }
 }
 
@@ -414,14 +427,16 @@ cudaError_t launch_corr_tc(const CorrArgs& a, cudaStream_t st) {
   const long long warps = (npen + 31) / 32 * ax.S * 2;
   const unsigned blocks = (unsigned)((warps + 3) / 4);
   const int t = a.g.t;
-  if (t <= 8)
-    k_corr_tc<8><<<blocks, 128, 0, st>>>(a);
+  if (t == 8)
+    k_corr_tc<8, 8><<<blocks, 128, 0, st>>>(a);
+  else if (t <= 8)
+    k_corr_tc<8, 0><<<blocks, 128, 0, st>>>(a);
   else if (t <= 16)
-    k_corr_tc<16><<<blocks, 128, 0, st>>>(a);
+    k_corr_tc<16, 0><<<blocks, 128, 0, st>>>(a);
   else if (t <= 24)
-    k_corr_tc<24><<<blocks, 128, 0, st>>>(a);
+    k_corr_tc<24, 0><<<blocks, 128, 0, st>>>(a);
   else
-    k_corr_tc<32><<<blocks, 128, 0, st>>>(a);
+    k_corr_tc<32, 0><<<blocks, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -790,10 +805,76 @@ cudaError_t launch_shell(const ShellArgs& a, int blocks, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// The plain form: one launch per step of Eq. wavesim_iter over the whole grid.
+// A block walks grid rows (i0, i1); its threads take the row's axis-2 positions.
+// Corrections (C) are valid on the boundary-layer voxels only.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(256) k_plain_step(const __grid_constant__ PlainArgs a) {
+  __shared__ double red[8];
+  const long long N1 = a.g.N1, N2 = a.g.N2, rows = a.g.N0 * N1;
+  double acc = 0.0;
+  for (long long rho = blockIdx.x; rho < rows; rho += gridDim.x) {
+    const long long i0 = rho / N1, i1 = rho - i0 * N1;
+    const bool lay01 = a.tb.shell[0][i0] | a.tb.shell[1][i1];
+    const bool srow = a.S && i0 >= a.sbox[0] && i0 < a.sbox[1] && i1 >= a.sbox[2] && i1 < a.sbox[3];
+    const long long rb = rho * N2;
+    float racc = 0.f;
+    for (long long i2 = threadIdx.x; i2 < N2; i2 += blockDim.x) {
+      const long long v = rb + i2;
+      const bool lay = lay01 || a.tb.shell[2][i2];
+      if (MODE == PLAIN_U) {
+        float2 u = cmul(a.B[v], a.X[v]);
+        if (lay) u = csub(u, a.C[v]);
+        if (srow && i2 >= a.sbox[4] && i2 < a.sbox[5]) u = cadd(u, cmul(a.mc, a.S[v]));
+        a.K[v] = u;
+      } else if (MODE == PLAIN_PROP) {
+        const float p2 = a.tb.p2[0][i0] + a.tb.p2[1][i1] + a.tb.p2[2][i2];
+        // c (k0^2 - |p|^2) + 1
+        const float2 den = make_float2(fmaf(-a.c.x, p2, a.ck0.x) + 1.f, fmaf(-a.c.y, p2, a.ck0.y));
+        const float inv = 1.f / (den.x * den.x + den.y * den.y);
+        a.K[v] = cmul(a.K[v], make_float2(den.x * inv, -den.y * inv));
+      } else if (MODE == PLAIN_D) {
+        a.K[v] = csub(a.X[v], a.K[v]);
+      } else if (MODE == PLAIN_R) {
+        float2 r = cmul(a.B[v], a.K[v]);
+        if (lay) r = csub(r, a.C[v]);
+        a.K[v] = r;
+      } else if (MODE == PLAIN_NORM) {
+        const float2 r = a.K[v];
+        racc = fmaf(r.x, r.x, fmaf(r.y, r.y, racc));
+      } else {
+        const float2 r = a.K[v], x = a.X[v];
+        a.X[v] = make_float2(fmaf(-a.alpha, r.x, x.x), fmaf(-a.alpha, r.y, x.y));
+      }
+    }
+    if (MODE == PLAIN_NORM) acc += (double)racc;  // FP32 over at most N2 / 256 voxels, then FP64
+  }
+  if (MODE == PLAIN_NORM) {
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
+  }
+}
+
+cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t st) {
+  switch (a.mode) {
+    case PLAIN_U: k_plain_step<PLAIN_U><<<kPlainBlocks, 256, 0, st>>>(a); break;
+    case PLAIN_PROP: k_plain_step<PLAIN_PROP><<<kPlainBlocks, 256, 0, st>>>(a); break;
+    case PLAIN_D: k_plain_step<PLAIN_D><<<kPlainBlocks, 256, 0, st>>>(a); break;
+    case PLAIN_R: k_plain_step<PLAIN_R><<<kPlainBlocks, 256, 0, st>>>(a); break;
+    case PLAIN_NORM: k_plain_step<PLAIN_NORM><<<kPlainBlocks, 256, 0, st>>>(a); break;
+    case PLAIN_UPD: k_plain_step<PLAIN_UPD><<<kPlainBlocks, 256, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 __global__ void k_state_arm(DevState* st, int add_iter, double tol, int reset, int hist_cap) {
   if (reset) {
     st->iter = 0;
     st->R0 = 0.0;
+    st->r0_fixed = 0;
     st->eps = 1.0;
     st->best = 1e300;
     st->rise = 0;

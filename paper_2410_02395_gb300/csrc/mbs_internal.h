@@ -52,6 +52,7 @@ struct DevState {
   int status;     // 0, or MBS_ENAN / MBS_EDIVERGE
   double tol;
   double R0;      // ||r_0||^2
+  int r0_fixed;   // 1: R0 was set from x = 0 before a warm start (not from the first iteration)
   double eps;     // last relative residual
   double best;    // smallest eps so far (divergence guard)
   int rise;       // consecutive iterations with eps > 4 * best
@@ -135,6 +136,33 @@ struct ShellArgs {
   int mode;
   const float2* cW;     // c W (t x t), for the fused axis-2 corrections of launch_shell_rows
 };
+
+// One step of the plain form of the iteration (MBS_FLAG_PLAIN_STEPS): every
+// step of Eq. wavesim_iter is its own launch over the whole grid.
+enum PlainMode {
+  PLAIN_U = 0,     // K = B x + y - E x           (E x in C on the boundary layers)
+  PLAIN_PROP = 1,  // K *= 1 / (c (k0^2 - |p|^2) + 1)  (in k-space, unscaled)
+  PLAIN_D = 2,     // K = x - K                   (d = x - w)
+  PLAIN_R = 3,     // K = B K - E d               (E d in C on the boundary layers)
+  PLAIN_NORM = 4,  // partials[block] = sum |K|^2 (FP64 per block)
+  PLAIN_UPD = 5    // x -= alpha K
+};
+struct PlainArgs {
+  float2* K;
+  float2* X;
+  const float2* B;
+  const float2* C;
+  const float2* S;
+  int64_t sbox[6];
+  float2 mc, c, ck0;
+  float alpha;
+  AxisTables tb;
+  GridDesc g;
+  double* partials;
+  int mode;
+};
+constexpr int kPlainBlocks = 152 * 8;
+cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t st);
 
 // Launchers (return cudaGetLastError of the launch).
 cudaError_t launch_rows_first(int n, const PassArgs& a, int nrows_blocks, cudaStream_t st);

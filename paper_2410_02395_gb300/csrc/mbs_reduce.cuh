@@ -30,7 +30,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // Update of the solver state from the summed |r_n|^2 (thread 0 only).
 __device__ __forceinline__ void state_update(DevState* st, double R, double* hist) {
   const int it = st->iter;
-  if (it == 0) st->R0 = R;
+  if (it == 0 && !st->r0_fixed) st->R0 = R;
   const double eps = st->R0 > 0.0 ? sqrt(R / st->R0) : 0.0;
   if (hist && it < st->hist_cap) hist[it] = eps;
   st->eps = eps;

@@ -67,14 +67,17 @@ CASES = {
 
 TF32_CASES = ["cube_2x2x2", "uneven_sizes", "single_nonperiodic", "periodic_split_seam", "t_sweep_6", "prime_sizes"]
 RES_CASES = ["cube_2x2x2", "single_periodic", "ragged_3x1x2", "line_1d", "t8_2x2x2", "t_sweep_16", "prime_sizes"]
+PLAIN_CASES = ["cube_2x2x2", "uneven_sizes", "periodic_split_seam", "t8_2x2x2", "prime_sizes", "single_periodic"]
 
 
 @pytest.fixture(scope="module", params=sorted(CASES) + ["tf32:" + c for c in TF32_CASES] +
-                ["res:" + c for c in RES_CASES])
+                ["res:" + c for c in RES_CASES] + ["plain:" + c for c in PLAIN_CASES])
 def pair(request):
     """(plan, oracle) on one case; "tf32:" cases run the edge corrections as 3xTF32
     tensor-core products (same tolerances: the split recovers FP32 accuracy);
-    "res:" cases iterate in the residual form (same iterates in exact arithmetic)."""
+    "res:" cases iterate in the residual form (same iterates in exact arithmetic);
+    "plain:" cases iterate in the one-launch-per-step form with the stop test on
+    the host."""
     name = request.param
     kw = {}
     if name.startswith("tf32:"):
@@ -83,6 +86,9 @@ def pair(request):
     if name.startswith("res:"):
         name = name[4:]
         kw["residual_form"] = True
+    if name.startswith("plain:"):
+        name = name[6:]
+        kw["plain_steps"] = True
     plan, ref, n = make_pair(**CASES[name], **kw)
     yield plan, ref
     plan.close()
@@ -293,3 +299,61 @@ def test_out_of_memory_is_reported_without_allocating():
     assert not h.value
     free1, _ = torch.cuda.mem_get_info()
     assert abs(free1 - free0) < (64 << 20)
+
+
+def test_plain_steps_form_solves_like_the_fused_form():
+    """The one-launch-per-step form (host-side residual sums and stop test) stops
+    at the same iteration as the fused form and the oracle, with the same field."""
+    kw = dict(split=(2, 2, 1), widths=((3, 3), (3, 3), (2, 2)), t=4, seed=9)
+    plan, ref, n = make_pair((24, 20, 16), plain_steps=True, **kw)
+    fused, _, _ = make_pair((24, 20, 16), **kw)
+    src = torch.from_numpy(point_source(ref.shape)).cuda()
+    x, it, res, hist = plan.solve(src, tol=1e-4, max_iter=5000, with_history=True)
+    xf, itf, resf = fused.solve(src, tol=1e-4, max_iter=5000)
+    xr, itr, _ = ref.solve(point_source(ref.shape), tol=1e-4, max_iter=5000)
+    assert it == itf and abs(it - itr) <= 1 and res < 1e-4
+    assert relative_l2(x.cpu().numpy(), xf.cpu().numpy()) < 1e-4
+    assert len(hist) == it and hist[0] == 1.0
+    plan.close()
+    fused.close()
+
+
+def test_plain_steps_form_refuses_the_residual_form_and_batches():
+    pkg = _pkg()
+    with pytest.raises(pkg.MBSError) as ei:
+        make_pair((16, 16, 16), split=(2, 1, 1), t=2, plain_steps=True, residual_form=True)
+    assert ei.value.status == 1
+    plan, _, _ = make_pair((16, 16, 16), split=(2, 1, 1), t=2, plain_steps=True)
+    with pytest.raises(pkg.MBSError) as ei:
+        pkg.Batch([plan])
+    assert ei.value.status == 1
+    plan.close()
+
+
+@pytest.mark.parametrize("form", ["x", "residual", "plain"])
+def test_warm_start_resumes_the_oracle_iteration(form):
+    """Resume (Sec. 3.1: MBS converges from any start): 10 oracle iterations, then
+    the GPU continues from that field for 10 more; the field and the residual
+    history equal the oracle's iterations 11-20 (eps normalised by ||Gamma^-1 y||)."""
+    kw = {"residual_form": form == "residual", "plain_steps": form == "plain"}
+    plan, ref, n = make_pair((32, 24, 20), split=(2, 2, 1), widths=((3, 3), (3, 3), (2, 2)), t=4, seed=17, **kw)
+    src = point_source(ref.shape)
+    x10, _, _ = ref.solve(src, tol=0.0, max_iter=10)
+    x20, _, hist20 = ref.solve(src, tol=0.0, max_iter=20)
+    plan.set_source(torch.from_numpy(src).cuda())
+    plan.set_initial_field(torch.from_numpy(x10.astype(np.complex64)).cuda())
+    st, it, eps = plan.iterate(10, 0.0)
+    assert it == 10
+    x = plan.field(like=torch.zeros(1, device="cuda"))
+    assert relative_l2(x.cpu().numpy(), x20) < ITER_TOL
+    np.testing.assert_allclose(plan.history(10), hist20[10:], rtol=1e-4, atol=1e-6)
+    plan.close()
+
+
+def test_warm_start_needs_a_source():
+    pkg = _pkg()
+    plan, ref, n = make_pair((16, 16, 16), split=(2, 1, 1), t=2, seed=4)
+    with pytest.raises(pkg.MBSError) as ei:
+        plan.set_initial_field(np.zeros(ref.shape, np.complex64))
+    assert ei.value.status == 1
+    plan.close()
