@@ -76,7 +76,11 @@ typedef enum mbs_operator {
 
 /* Limits of this build. */
 #define MBS_MAX_SPLIT 16 /* subdomains per axis */
-#define MBS_MAX_T 32     /* truncation width; compiled values t = 1..16, 20, 24, 32 */
+#define MBS_MAX_T 40     /* truncation width (Fig. 7 sweeps t = 0..40): every t in 1..40; widths
+                            1..16, 20, 24 and 32 have specialised correction kernels, the others a
+                            generic one (the tensor-core form takes t <= 32) */
+#define MBS_T_NONE (-1)  /* mbs_options.truncation value for t = 0: no edge corrections at all
+                            (uncoupled periodic subdomains; the t = 0 end of Fig. 7)        */
 #define MBS_MAX_EDGE 512 /* longest subdomain edge. Edges <= 512 whose prime factors are 2, 3,
                             5 and 7 have mixed-radix FFT kernels (106 lengths); any other edge
                             <= 256 is transformed by Bluestein's algorithm on one of them */
@@ -95,13 +99,14 @@ typedef enum mbs_operator {
                                         arithmetic; in complex64 the residual has no floor set by ||x||,
                                         so tolerances below that floor are reachable. Costs about
                                         24 B per voxel and iteration more (x and its low word).      */
-#define MBS_FLAG_NO_TMA (1u << 3) /* feed the axis-1 FFT passes with per-thread global loads instead
-                                     of tensor-map (TMA) copies into double-buffered shared memory.
-                                     Default: TMA where the edge has TMA kernels (32, 64, 128, 256)
-                                     and the grid's row pitch is a multiple of 16 bytes.          */
+#define MBS_FLAG_NO_TMA (1u << 3) /* feed the axis-1 and axis-0 FFT passes with per-thread global
+                                     loads instead of tensor-map (TMA) copies into double-buffered
+                                     shared memory. Default: TMA where the edge has TMA kernels
+                                     (32, 64, 128, 256, 320), the grid's row pitch is a multiple of
+                                     16 bytes and the plan-time timing finds TMA faster.          */
 #define MBS_FLAG_FORCE_TMA (1u << 4) /* keep every tensor-map feed the plan can build instead of timing
-                                     the TMA-fed against the register-fed axis-1 pass at plan
-                                     creation and keeping the faster (results are identical)      */
+                                     the TMA-fed against the register-fed pass at plan creation and
+                                     keeping the faster (results are identical)                   */
 #define MBS_FLAG_PLAIN_STEPS (1u << 5) /* comparison form of the iteration: every step of
                                      Eq. wavesim_iter is its own launch over the whole grid (E x,
                                      u = B x + y - E x, three forward FFT passes, the propagator,
@@ -112,7 +117,8 @@ typedef enum mbs_operator {
                                      FP32 rounding; not with MBS_FLAG_RESIDUAL_FORM or in batches. */
 
 typedef struct mbs_options {
-  int32_t truncation;        /* t, the kept edge width (Sec. 3, Fig. 5); 0 -> 8 (Sec. 3.3)      */
+  int32_t truncation;        /* t, the kept edge width (Sec. 3, Fig. 5); 0 -> 8 (Sec. 3.3);
+                                MBS_T_NONE -> t = 0                                              */
   double alpha;              /* relaxation (Eq. c_scale); 0 -> 0.75                              */
   uint32_t periodic_mask;    /* bit d set: axis d periodic. Periodic unsplit axis: no corrections
                                 (a_d = 0); periodic split axis: transfer across the seam (a_d = 2) */
@@ -172,8 +178,9 @@ typedef struct mbs_plan_info {
   int64_t sizes[3][MBS_MAX_SPLIT];  /* subdomain edges along each axis                        */
   size_t device_bytes;       /* device memory held by the plan                                 */
   int32_t graph_iters;
-  int32_t tma_groups;        /* axis-1 edge groups whose pass is fed by TMA (chosen at plan
-                                creation by timing both feeds; results are identical)          */
+  int32_t tma_groups;        /* edge groups whose axis-1 pass or axis-0 (forward, multiplier,
+                                inverse) pass is fed by TMA (chosen at plan creation by timing
+                                both feeds; results are identical)                             */
 } mbs_plan_info;
 
 MBS_API mbs_status mbs_plan_get_info(const mbs_plan *plan, mbs_plan_info *info);

@@ -166,7 +166,7 @@ class Plan:
         self.shape = tuple(int(s) for s in shape)
         opts = _Options()
         self.lib.mbs_default_options(C.byref(opts))
-        opts.truncation = int(truncation)
+        opts.truncation = -1 if int(truncation) == 0 else int(truncation)  # t = 0: MBS_T_NONE
         opts.alpha = float(alpha)
         opts.periodic_mask = sum((1 << d) for d in range(3) if periodic[d])
         opts.absorb_kappa = float(kappa)
@@ -210,7 +210,7 @@ class Plan:
         lib = load_library()
         opts = _Options()
         lib.mbs_default_options(C.byref(opts))
-        opts.truncation = int(truncation)
+        opts.truncation = -1 if int(truncation) == 0 else int(truncation)  # t = 0: MBS_T_NONE
         opts.flags = 4 if residual_form else 0
         keep = None
         if split_sizes is not None:

@@ -281,10 +281,12 @@ mbs_status validate_and_fill(mbs_plan* p, const int64_t shape[3], double h, doub
     return fail(MBS_EINVAL, "pixel size and wavelength must be positive and finite");
   p->h = h;
   p->lambda = lambda;
-  p->t = (o && o->truncation > 0) ? o->truncation : 8;
-  if (o && o->truncation < 0) return fail(MBS_EINVAL, "truncation must be >= 0");
+  if (o && o->truncation < MBS_T_NONE) return fail(MBS_EINVAL, "truncation must be >= 0 or MBS_T_NONE");
+  p->t = !o ? 8 : (o->truncation == MBS_T_NONE ? 0 : (o->truncation > 0 ? o->truncation : 8));
   if (p->t > kMaxT) return fail(MBS_EINVAL, "truncation exceeds MBS_MAX_T");
-  if (!corr_t_supported(p->t)) return fail(MBS_EUNSUPPORTED, "truncation t must be 1..16, 20, 24 or 32");
+  if (!corr_t_supported(p->t)) return fail(MBS_EUNSUPPORTED, "no edge-correction kernel for this truncation");
+  if (o && (o->flags & MBS_FLAG_CORR_TF32) && p->t > 32)
+    return fail(MBS_EUNSUPPORTED, "tensor-core corrections need t <= 32");
   p->alpha = (o && o->alpha > 0.0) ? o->alpha : 0.75;
   p->kappa = (o && o->absorb_kappa >= 0.0) ? o->absorb_kappa : 0.5;
   p->periodic = o ? o->periodic_mask : 0u;
@@ -641,22 +643,35 @@ cudaError_t run_corr(mbs_plan* p, const float2* F, float2* C, const DevState* st
   return run_corr_rec(p, F, C, state, nullptr, 0, axis2);
 }
 
-// Axis-1 pass of one edge group: TMA-fed where the plan has a tensor map for
-// it, register-fed otherwise. (A TMA-fed axis-0 pass, forward transform,
-// propagator and inverse per tile, measured slower than the register-fed one at
-// four CTAs per SM, 78.9 against 76.1 us on the 256^3 workload: it is
-// issue-bound, not waiting on memory.)
+// Axis-1 pass of one edge group: TMA-fed where the plan kept a tensor map for
+// it, register-fed otherwise.
 cudaError_t strided_pass(const mbs_plan* p, const PassArgs& a, int n, bool inv) {
   auto it = p->tmaps.find(1 * 65536 + n);
   if (it != p->tmaps.end()) return launch_strided_tma(n, 1, inv, a, it->second, p->stream);
   return launch_strided(n, 1, inv, a, p->stream);
 }
 
-// Plan-time choice between the TMA-fed and the register-fed axis-1 pass of each
-// edge group: both run the same arithmetic (bit-identical results), so the
-// plan times both on its own geometry (forward and inverse, 2 warm-up and 5
-// timed launches each, CUDA events on the plan's stream; the FFT buffer's
-// contents do not matter) and keeps the tensor map only where TMA is faster.
+// Axis-0 pass of one edge group (a.mode: MID_PROP, MID_LSYM, MID_FWD, MID_INV):
+// the forward-multiplier-inverse modes are TMA-fed where the plan kept a tensor
+// map for the edge (at 128 the register-fed kernel at four CTAs per SM is
+// issue-bound and faster, 76.1 against 78.9 us on the 256^3 workload; at 320,
+// one CTA per SM, the prefetching feed pays).
+cudaError_t mid_pass(const mbs_plan* p, const PassArgs& a, int n) {
+  if (a.mode == MID_PROP || a.mode == MID_LSYM) {
+    auto it = p->tmaps.find(0 * 65536 + n);
+    if (it != p->tmaps.end()) return launch_mid_tma(n, a, it->second, p->stream);
+  }
+  return launch_mid(n, a, p->stream);
+}
+
+// Plan-time choice between the TMA-fed and the register-fed axis-1 and axis-0
+// passes of each edge group: both forms run the same arithmetic (bit-identical
+// results), so the plan times both on its own geometry (axis 1 forward and
+// inverse, axis 0 with the propagator; CUDA events on the plan's stream; the
+// FFT buffer's contents do not matter): 2 warm-up launches of each form, then
+// three rounds that alternate the forms, 3 launches per form and round, the
+// fastest round of each form counting; the tensor map is kept only where TMA
+// is faster.
 mbs_status autotune_strided(mbs_plan* p) {
   if (p->tmaps.empty() || (p->flags & MBS_FLAG_FORCE_TMA)) return MBS_OK;
   cudaEvent_t e0, e1;
@@ -666,28 +681,36 @@ mbs_status autotune_strided(mbs_plan* p) {
   a.state = p->free_state;
   a.tma_wait = 0;  // the full bound: a caller's short bound is for the iteration and the operators
   std::vector<int> drop;
-  for (auto& gy : p->groups[1]) {
-    auto it = p->tmaps.find(1 * 65536 + gy.n);
-    if (it == p->tmaps.end()) continue;
-    a.nsub = gy.nsub;
-    memcpy(a.subs, gy.subs, sizeof(a.subs));
-    set_len_tables(p, a, gy.n);
-    float ms[2] = {0.f, 0.f};
-    for (int v = 0; v < 2; v++) {
-      auto launch = [&](bool inv) {
+  for (int axis = 0; axis < 2; axis++) {
+    for (auto& gy : p->groups[axis]) {
+      auto it = p->tmaps.find(axis * 65536 + gy.n);
+      if (it == p->tmaps.end()) continue;
+      a.nsub = gy.nsub;
+      memcpy(a.subs, gy.subs, sizeof(a.subs));
+      set_len_tables(p, a, gy.n);
+      a.mode = MID_PROP;
+      float best[2] = {1e30f, 1e30f};
+      auto launch = [&](int v, bool inv) -> cudaError_t {
+        if (axis == 0)
+          return v == 0 ? launch_mid_tma(gy.n, a, it->second, p->stream) : launch_mid(gy.n, a, p->stream);
         return v == 0 ? launch_strided_tma(gy.n, 1, inv, a, it->second, p->stream)
                       : launch_strided(gy.n, 1, inv, a, p->stream);
       };
-      for (int r = 0; r < 2; r++)
-        if (launch(false) || launch(true)) return fail(MBS_ECUDA, "axis-1 pass timing launch failed");
-      CU(cudaEventRecord(e0, p->stream));
-      for (int r = 0; r < 5; r++)
-        if (launch(false) || launch(true)) return fail(MBS_ECUDA, "axis-1 pass timing launch failed");
-      CU(cudaEventRecord(e1, p->stream));
-      CU(cudaEventSynchronize(e1));
-      CU(cudaEventElapsedTime(&ms[v], e0, e1));
+      for (int v = 0; v < 2; v++)
+        if (launch(v, false) || launch(v, true)) return fail(MBS_ECUDA, "pass timing launch failed");
+      for (int round = 0; round < 3; round++)
+        for (int v = 0; v < 2; v++) {
+          CU(cudaEventRecord(e0, p->stream));
+          for (int r = 0; r < 3; r++)
+            if (launch(v, false) || launch(v, true)) return fail(MBS_ECUDA, "pass timing launch failed");
+          CU(cudaEventRecord(e1, p->stream));
+          CU(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CU(cudaEventElapsedTime(&ms, e0, e1));
+          best[v] = std::min(best[v], ms);
+        }
+      if (best[1] < best[0]) drop.push_back(it->first);
     }
-    if (ms[1] < ms[0]) drop.push_back(it->first);
   }
   for (int k : drop) p->tmaps.erase(k);
   cudaEventDestroy(e0);
@@ -726,7 +749,7 @@ cudaError_t run_transform_chain(mbs_plan* p, PassArgs a, int first_mode, int mid
     memcpy(a.subs, gx.subs, sizeof(a.subs));
     set_len_tables(p, a, gx.n);
     if (rec) rec->begin(KK_MID);
-    e = launch_mid(gx.n, a, p->stream);
+    e = mid_pass(p, a, gx.n);
     if (rec) rec->end();
     if (e) return e;
   }
@@ -1139,10 +1162,11 @@ mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double p
   st = upload_tables(p);
   if (st) return cleanup(st);
   if (!(p->flags & MBS_FLAG_NO_TMA)) {
-    for (auto& gsz : p->groups[1]) {
-      CUtensorMap tm;
-      if (gsz.n > 1 && make_tma_map(&tm, p->K, p->g, 1, gsz.n)) p->tmaps[1 * 65536 + gsz.n] = tm;
-    }
+    for (int axis = 0; axis < 2; axis++)
+      for (auto& gsz : p->groups[axis]) {
+        CUtensorMap tm;
+        if (gsz.n > 1 && make_tma_map(&tm, p->K, p->g, axis, gsz.n)) p->tmaps[axis * 65536 + gsz.n] = tm;
+      }
   }
   // refractive index: use the device array directly, or stage it through src
   const float2* n_dev = nullptr;

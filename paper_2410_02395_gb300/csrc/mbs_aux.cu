@@ -392,6 +392,77 @@ __global__ void __launch_bounds__(128) k_corr_tc(const __grid_constant__ CorrArg
   }
 }
 
+// Any t (1..kMaxT) on any axis, for the widths without a compiled kernel: one
+// thread per (pencil, subdomain) does both sides, reading its inputs from
+// global memory for every term (O(t^2) cached loads; widths above 32 are for
+// the truncation sweep of Fig. 7 only). Both sides run in the same thread, so a
+// voxel in both ranges (n < 2t) gets both terms without a race.
+__global__ void __launch_bounds__(128) k_corr_generic(const __grid_constant__ CorrArgs a) {
+  __shared__ float w[2 * kMaxT];
+  if (a.state && a.state->done) return;
+  const int t = a.g.t;
+  if (threadIdx.x < 2 * t - 1) {
+    const int m = threadIdx.x, aa = m < t - 1 ? t - 1 - m : 0, bb = aa + m - (t - 1);
+    w[m] = a.cW[aa * t + bb].y;
+  }
+  __syncthreads();
+  const int d = a.axis;
+  const AxisDesc& ax = a.g.ax[d];
+  const long long N0 = a.g.N0, N1 = a.g.N1, N2 = a.g.N2;
+  const long long npen = d == 0 ? N1 * N2 : (d == 1 ? N0 * N2 : N0 * N1);
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= npen * ax.S) return;
+  const int s = (int)(gid / npen);
+  const long long p = gid - (long long)s * npen;
+  long long base, stride;
+  bool add = false;
+  if (d == 0) {
+    base = p;
+    stride = N1 * N2;
+  } else if (d == 1) {
+    const long long i0 = p / N2, i2 = p - i0 * N2;
+    base = i0 * N1 * N2 + i2;
+    stride = N2;
+    add = a.tb.shell[0][i0];
+  } else {
+    const long long i0 = p / N1, i1 = p - i0 * N1;
+    base = p * N2;
+    stride = 1;
+    add = a.tb.shell[0][i0] || a.tb.shell[1][i1];
+  }
+  const int off = ax.off[s], n = ax.n[s];
+  const int L = ax.left[s], R = ax.right[s];
+  const float2* __restrict__ F = a.F;
+  float2* C = a.C;
+  auto at = [&](int pos) { return F[base + (long long)pos * stride]; };
+  // first t layers: out[q] = sum_b w[q - b + t - 1] (f_left[n_l - t + b] - f_s[n - t + b])
+  for (int q = 0; q < t; q++) {
+    float vx = 0.f, vy = 0.f;
+    for (int b = 0; b < t; b++) {
+      float2 f = at(off + n - t + b);
+      f = make_float2(-f.x, -f.y);
+      if (L >= 0) f = cadd(f, at(ax.off[L] + ax.n[L] - t + b));
+      vx = fmaf(w[q - b + t - 1], f.x, vx);
+      vy = fmaf(w[q - b + t - 1], f.y, vy);
+    }
+    put(C, base + (long long)(off + q) * stride, times_i(vx, vy), add);
+  }
+  // last t layers: out[n - t + aa] = sum_b w[b - aa + t - 1] (f_right[b] - f_s[b])
+  for (int aa = 0; aa < t; aa++) {
+    float vx = 0.f, vy = 0.f;
+    for (int b = 0; b < t; b++) {
+      float2 f = at(off + b);
+      f = make_float2(-f.x, -f.y);
+      if (R >= 0) f = cadd(f, at(ax.off[R] + b));
+      vx = fmaf(w[b - aa + t - 1], f.x, vx);
+      vy = fmaf(w[b - aa + t - 1], f.y, vy);
+    }
+    const int q = n - t + aa;
+    // a voxel also in the first range (n < 2t) was written just above by this thread
+    put(C, base + (long long)(off + q) * stride, times_i(vx, vy), add || q < t);
+  }
+}
+
 template <int T>
 cudaError_t launch_corr_t(const CorrArgs& a, cudaStream_t st) {
   const AxisDesc& ax = a.g.ax[a.axis];
@@ -419,7 +490,9 @@ cudaError_t launch_corr_t(const CorrArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-bool corr_t_supported(int t) { return (t >= 1 && t <= 16) || t == 20 || t == 24 || t == 32; }
+// Widths with specialised kernels: 1..16, 20, 24, 32; any other t up to kMaxT
+// takes k_corr_generic (t = 0 has no corrections at all).
+bool corr_t_supported(int t) { return t >= 0 && t <= kMaxT; }
 
 cudaError_t launch_corr_tc(const CorrArgs& a, cudaStream_t st) {
   const AxisDesc& ax = a.g.ax[a.axis];
@@ -455,8 +528,13 @@ cudaError_t launch_corr(const CorrArgs& a, cudaStream_t st) {
     MBS_T(9) MBS_T(10) MBS_T(11) MBS_T(12) MBS_T(13) MBS_T(14) MBS_T(15) MBS_T(16)
     MBS_T(20) MBS_T(24) MBS_T(32)
 #undef MBS_T
-    default:
-      return cudaErrorInvalidValue;
+    default: {
+      if (a.g.t < 1 || a.g.t > kMaxT) return cudaErrorInvalidValue;
+      const AxisDesc& ax = a.g.ax[a.axis];
+      const long long npen = a.axis == 0 ? a.g.N1 * a.g.N2 : (a.axis == 1 ? a.g.N0 * a.g.N2 : a.g.N0 * a.g.N1);
+      k_corr_generic<<<(unsigned)((npen * ax.S + 127) / 128), 128, 0, st>>>(a);
+      return cudaGetLastError();
+    }
   }
 }
 

@@ -8,7 +8,7 @@
 namespace mbs {
 
 constexpr int kMaxSplit = 16;   // subdomains per axis
-constexpr int kMaxT = 32;       // truncation width t
+constexpr int kMaxT = 40;       // truncation width t
 constexpr int kMaxFFT = 512;    // longest subdomain edge handled by the FFT engine
 
 // One axis of the block decomposition (Sec. 3: subdomains along any axis, of
@@ -175,6 +175,9 @@ cudaError_t launch_mid(int n, const PassArgs& a, cudaStream_t st);
 bool tma_len_supported(int n);
 bool make_tma_map(CUtensorMap* tm, void* K, const GridDesc& g, int axis, int n);
 cudaError_t launch_strided_tma(int n, int axis, bool inv, const PassArgs& a, const CUtensorMap& tm, cudaStream_t st);
+// TMA-fed axis-0 pass (forward transform, propagator or symbol of L, inverse):
+// modes MID_PROP and MID_LSYM, tensor map made with axis 0.
+cudaError_t launch_mid_tma(int n, const PassArgs& a, const CUtensorMap& tm, cudaStream_t st);
 // Bluestein FFT lengths: the M of the convolution for edge n (0: n has no
 // compiled Bluestein form), and the launcher the dispatch falls back to.
 int bluestein_len(int n);

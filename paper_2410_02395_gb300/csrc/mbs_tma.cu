@@ -7,8 +7,9 @@
 
 namespace mbs {
 
-// Edge lengths with TMA-fed kernels (a tile box is at most 256 along an axis).
-#define MBS_TMA_SIZES(X) X(32) X(64) X(128) X(256)
+// Edge lengths with TMA-fed kernels (a box is at most 256 along an axis: the
+// 320 tile is two boxes of 160).
+#define MBS_TMA_SIZES(X) X(32) X(64) X(128) X(256) X(320)
 
 bool tma_len_supported(int n) {
   switch (n) {
@@ -48,7 +49,8 @@ bool make_tma_map(CUtensorMap* tm, void* K, const GridDesc& g, int axis, int n) 
   const cuuint64_t dims[3] = {(cuuint64_t)g.N2, (cuuint64_t)g.N1, (cuuint64_t)g.N0};
   const cuuint64_t strides[2] = {(cuuint64_t)g.N2 * 8, (cuuint64_t)g.N1 * g.N2 * 8};
   if (strides[0] % 16 || strides[1] % 16 || ((uintptr_t)K % 16)) return false;
-  const cuuint32_t box[3] = {32, axis == 1 ? (cuuint32_t)n : 1u, axis == 0 ? (cuuint32_t)n : 1u};
+  const cuuint32_t bl = (cuuint32_t)tma_box_len(n);
+  const cuuint32_t box[3] = {32, axis == 1 ? bl : 1u, axis == 0 ? bl : 1u};
   const cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, K, dims, strides, box, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -92,11 +94,16 @@ static cudaError_t run_tma(int kind, int axis, bool inv, const PassArgs& a, cons
   e = set_smem(KER, smem);                                       \
   if (e) return e;                                               \
   KER<<<persistent_blocks(KER, threads, smem, ntiles), threads, smem, st>>>(a, tm);
-  if (axis != 1) return cudaErrorInvalidValue;  // the axis-0 pass is register-fed (see strided_pass)
-  if (inv) {
-    MBS_TMA_LAUNCH((k_strided_tma<N, 1, true>))
+  if (kind == 3) {  // axis-0 pass: forward, multiplier, inverse
+    if (axis != 0) return cudaErrorInvalidValue;
+    MBS_TMA_LAUNCH((k_mid_tma<N>))
   } else {
-    MBS_TMA_LAUNCH((k_strided_tma<N, 1, false>))
+    if (axis != 1) return cudaErrorInvalidValue;
+    if (inv) {
+      MBS_TMA_LAUNCH((k_strided_tma<N, 1, true>))
+    } else {
+      MBS_TMA_LAUNCH((k_strided_tma<N, 1, false>))
+    }
   }
 #undef MBS_TMA_LAUNCH
   return cudaGetLastError();
@@ -109,6 +116,19 @@ cudaError_t launch_strided_tma(int n, int axis, bool inv, const PassArgs& a, con
     return run_tma<n>(2, axis, inv, a, tm, st);
     MBS_TMA_SIZES(MBS_TMA_CASE)
 #undef MBS_TMA_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_mid_tma(int n, const PassArgs& a, const CUtensorMap& tm, cudaStream_t st) {
+  if (a.mode != MID_PROP && a.mode != MID_LSYM) return cudaErrorInvalidValue;
+  switch (n) {
+#define MBS_TMA_MID_CASE(n) \
+  case n:                   \
+    return run_tma<n>(3, 0, false, a, tm, st);
+    MBS_TMA_SIZES(MBS_TMA_MID_CASE)
+#undef MBS_TMA_MID_CASE
     default:
       return cudaErrorInvalidValue;
   }

@@ -1,9 +1,11 @@
-// Strided (axis-1) FFT passes fed by the Tensor Memory Accelerator.
+// Strided FFT passes fed by the Tensor Memory Accelerator: the axis-1 pass and
+// the axis-0 pass (forward transform, k-space multiplier, inverse transform).
 //
 // A tile is 32 consecutive axis-2 positions x one subdomain's n positions
-// along the pass axis (one i0, or one i1). It is a box of the 3-D tensor map
-// over the FFT buffer (dims N2, N1, N0; 8-byte elements), so one
-// cp.async.bulk.tensor brings the whole tile into shared memory as [n][32]
+// along the pass axis (one i0, or one i1). It is one box of the 3-D tensor map
+// over the FFT buffer (dims N2, N1, N0; 8-byte elements), or two boxes of n/2
+// when n is above 256 (a box is at most 256 long along an axis), so one or two
+// cp.async.bulk.tensor copies bring the whole tile into shared memory as [n][32]
 // (row e = element e of the 32 pencils; positions past N2 read as zeros).
 // Persistent CTAs walk the tiles with two buffers: the copy of the next tile
 // is in flight while the current one is transformed in place; the last radix
@@ -88,15 +90,23 @@ __device__ __forceinline__ TmaTile tma_tile(int t, int gx, int ny) {
   return r;
 }
 
-template <int AXIS>
+// Box length along the pass axis for edge n: n, or n/2 above 256.
+__host__ __device__ constexpr int tma_box_len(int n) { return n > 256 ? n / 2 : n; }
+
+template <int N, int AXIS>
 __device__ __forceinline__ void tma_issue(const PassArgs& a, const CUtensorMap* tm, const TmaTile& tl, float2* buf,
                                           uint64_t* bar, unsigned bytes) {
+  constexpr int BL = tma_box_len(N);
+  static_assert(N % BL == 0 && N / BL <= 2, "one or two boxes per tile");
   const int j = a.subs[tl.js];
   mbar_expect_tx(bar, bytes);
-  if (AXIS == 1)
-    tma_load_3d(buf, tm, tl.ib * 32, a.g.ax[1].off[j], tl.y, bar);
-  else
-    tma_load_3d(buf, tm, tl.ib * 32, tl.y, a.g.ax[0].off[j], bar);
+#pragma unroll
+  for (int h = 0; h < N / BL; h++) {
+    if (AXIS == 1)
+      tma_load_3d(buf + h * BL * 32, tm, tl.ib * 32, a.g.ax[1].off[j] + h * BL, tl.y, bar);
+    else
+      tma_load_3d(buf + h * BL * 32, tm, tl.ib * 32, tl.y, a.g.ax[0].off[j] + h * BL, bar);
+  }
 }
 
 __device__ __forceinline__ void tma_fail(const PassArgs& a) {
@@ -125,12 +135,12 @@ __device__ __forceinline__ void tma_tiles(const PassArgs& a, const CUtensorMap* 
   }
   __syncthreads();
   int t = blockIdx.x;
-  if (t < ntiles && tid == 0) tma_issue<AXIS>(a, tm, tma_tile(t, gx, ny), dyn, &bar[0], kBytes);
+  if (t < ntiles && tid == 0) tma_issue<N, AXIS>(a, tm, tma_tile(t, gx, ny), dyn, &bar[0], kBytes);
   for (int k = 0; t < ntiles; k++, t += gridDim.x) {
     const int b = k & 1;
     const int tn = t + gridDim.x;
     if (tid == 0) {
-      if (tn < ntiles) tma_issue<AXIS>(a, tm, tma_tile(tn, gx, ny), dyn + (b ^ 1) * N * 32, &bar[b ^ 1], kBytes);
+      if (tn < ntiles) tma_issue<N, AXIS>(a, tm, tma_tile(tn, gx, ny), dyn + (b ^ 1) * N * 32, &bar[b ^ 1], kBytes);
       const bool got = mbar_wait(&bar[b], (k >> 1) & 1, limit);
       if (!got) {
         tma_fail(a);
@@ -184,6 +194,53 @@ __global__ void __launch_bounds__(32 * warps_for(N), tma_min_blocks(N)) k_stride
       if (valid) K[base + e * stride] = v;
     };
     fft_run<N, W, INV, false, 0, 1, true, false>(warp, lane, sm, a.tw, sld, gst);
+  });
+}
+
+// Axis-0 pass fed by TMA: forward transform, the k-space multiplier of
+// k_mid_turn (the propagator 1/(c(k0^2 - |p|^2) + 1) or the symbol of L, scaled
+// by 1/(n0 n1 n2)) and the inverse transform of each tile, the last stage
+// storing straight to global memory.
+template <int N>
+__global__ void __launch_bounds__(32 * warps_for(N), tma_min_blocks(N)) k_mid_tma(const __grid_constant__ PassArgs a,
+                                                                 const __grid_constant__ CUtensorMap tm) {
+  constexpr int W = warps_for(N);
+  extern __shared__ __align__(1024) float2 dyn[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int ok;
+  if (a.state && a.state->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2* K = a.K;
+  const float2 c = a.c, ck0 = a.ck0;
+  const bool prop = a.mode == MID_PROP;
+  // c is purely imaginary (Eq. c_scale2), so Re c(k0^2 - |p|^2) = Re(c k0^2) for every p
+  const float dx = ck0.x, ex = dx + 1.f;
+  tma_tiles<N, 0>(a, &tm, dyn, bar, &ok, [&](float2 (*sm)[32], const TmaTile& tl) {
+    const int j = a.subs[tl.js];
+    const int off0 = a.g.ax[0].off[j];
+    const long long i1 = tl.y;
+    const long long i2 = (long long)tl.ib * 32 + lane;
+    const bool valid = i2 < a.g.N2;
+    const long long i2c = valid ? i2 : 0;
+    const long long base = (long long)off0 * a.g.N1 * a.g.N2 + i1 * a.g.N2 + i2;
+    const long long stride = a.g.N1 * a.g.N2;
+    const float pl = a.tb.p2[1][i1] + a.tb.p2[2][i2c];
+    const float sc = a.tb.invn[0][off0] * a.tb.invn[1][i1] * a.tb.invn[2][i2c];
+    const float* p20 = a.tb.p2[0] + off0;
+    auto sld = [&](int e) { return sm[e][lane]; };
+    auto gst = [&](int e, float2 v) {
+      if (valid) K[base + e * stride] = v;
+    };
+    auto mul = [&](int e, float2 v) {
+      const float p2 = __ldg(p20 + e) + pl;
+      const float dy = fmaf(-c.y, p2, ck0.y);  // Im c(k0^2 - |p|^2)
+      if (prop) {
+        const float inv = sc * __frcp_rn(fmaf(ex, ex, dy * dy));
+        return cmul(v, make_float2(ex * inv, -dy * inv));
+      }
+      return cmul(v, make_float2(dx * sc, dy * sc));
+    };
+    fft_fwd_mul_inv<N, W, true, false>(warp, lane, sm, a.tw, sld, gst, mul);
   });
 }
 

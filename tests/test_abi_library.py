@@ -103,8 +103,10 @@ def test_degenerate_and_limit_arguments(lib):
 
     assert status((0, 8, 8), (1, 1, 1)) == 1                 # empty grid
     assert status((8, 8, 8), (1, 9, 1)) == 1                 # more subdomains than voxels along an axis
-    assert status((8, 8, 8), (1, 1, 1), truncation=33) == 1  # t above MBS_MAX_T
-    assert status((64, 8, 8), (2, 1, 1), truncation=17) == 8  # t not among the compiled widths
+    assert status((8, 8, 8), (1, 1, 1), truncation=41) == 1  # t above MBS_MAX_T
+    assert status((64, 40, 40), (2, 1, 1), truncation=17) == 0  # a width without a specialised kernel
+    assert status((64, 8, 8), (2, 1, 1), truncation=0) == 0     # t = 0: no corrections
+    assert status((64, 40, 40), (2, 1, 1), truncation=33) == 1  # t above a subdomain edge (32)
     assert status((16 * 32, 8, 8), (16, 1, 1)) == 0          # MBS_MAX_SPLIT subdomains along an axis
     assert status((512, 8, 8), (1, 1, 1)) == 0               # MBS_MAX_EDGE
     assert status((1, 1, 1), (1, 1, 1), truncation=1) == 0   # a single voxel

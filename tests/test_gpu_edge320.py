@@ -64,3 +64,23 @@ def test_320_edge_iterations_match_oracle(oracle_runs, geom, form):
     assert err < ITER_TOL, err
     np.testing.assert_allclose(hist, histr, rtol=1e-4, atol=1e-6)
     plan.close()
+
+
+@pytest.mark.parametrize("geom", ["axis0", "axis1"])
+def test_320_edge_tma_passes_equal_register_fed_passes(oracle_runs, geom):
+    """The 320 tile of the TMA-fed passes is two boxes of 160; the axis-1 pass and
+    the axis-0 pass (forward, propagator, inverse) fed that way give the same
+    iterates, bit for bit, as the register-fed kernels."""
+    import paper_2410_02395_gb300 as pkg
+
+    n, src, _, _, _, _ = oracle_runs[geom]
+    shape = GEOMS[geom]
+    xs = []
+    for kw in ({"force_tma": True}, {"no_tma": True}):
+        plan = pkg.Plan(shape, 0.25, 1.0, torch.from_numpy(n).cuda(), boundary_widths=KW["widths"],
+                        split=KW["split"], truncation=KW["t"], graph_iters=5, **kw)
+        assert (plan.info()["tma_groups"] >= 1) == ("force_tma" in kw)
+        x, it, _ = plan.solve(torch.from_numpy(src).cuda(), tol=0.0, max_iter=10)
+        xs.append(x)
+        plan.close()
+    assert torch.equal(xs[0], xs[1])

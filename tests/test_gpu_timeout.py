@@ -29,7 +29,7 @@ def _plan(**kw):
 
 def test_expired_tma_wait_ends_the_solve_with_etimeout():
     pkg, n, plan = _plan(tma_wait_cycles=1)
-    assert plan.info()["tma_groups"] == 1
+    assert plan.info()["tma_groups"] >= 1
     src = torch.from_numpy(point_source(SHAPE)).cuda()
     with pytest.raises(pkg.MBSError) as ei:
         plan.solve(src, tol=0.0, max_iter=3)
@@ -54,7 +54,7 @@ def test_expired_tma_wait_in_an_operator_is_reported_and_the_plan_recovers():
 def test_full_bound_with_forced_tma_matches_the_oracle():
     """The same plan with the default bound: the TMA-fed passes give the oracle's iterates."""
     pkg, n, plan = _plan()
-    assert plan.info()["tma_groups"] == 1
+    assert plan.info()["tma_groups"] >= 1
     src = point_source(SHAPE)
     x, it, _ = plan.solve(torch.from_numpy(src).cuda(), tol=0.0, max_iter=10)
     ref = Problem(n, 0.25, 1.0, widths=KW["boundary_widths"], split=KW["split"], t=KW["truncation"])

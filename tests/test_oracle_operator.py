@@ -13,6 +13,9 @@ CASES = [
     ((9, 8, 6), (3, 2, 1), (False, True, False), 3, ((1, 2), (0, 0), (1, 0))),
     ((6, 6, 6), (1, 1, 1), (False, False, False), 3, ((1, 1), (1, 1), (1, 1))),
     ((8, 8, 8), (2, 2, 2), (True, False, True), 4, ((0, 0), (1, 1), (0, 0))),
+    # the ends of the truncation sweep (Fig. 7: t = 0..40)
+    ((12, 1, 1), (2, 1, 1), (False, True, True), 0, ((2, 2), (0, 0), (0, 0))),
+    ((100, 1, 1), (2, 1, 1), (False, True, True), 40, ((4, 4), (0, 0), (0, 0))),
 ]
 
 
