@@ -22,6 +22,8 @@ Printed JSON line (one, from rank 0):
   cpu_baseline the FP64 oracle timed on the host cores (all of them, and one
                thread) on a bounded sample of the workload's recipe
   workloads    value and mixed value of the other single-grid workloads (C2, C3)
+  activation   time to tolerance with and without subdomain activation on a long
+               domain with the source in its first subdomain
 
 With --gpus N > 1 (under torchrun) every rank runs an independent replica of
 the workload on its own GPU (the path has no data exchange on one GPU);
@@ -310,6 +312,43 @@ def run_reference(args):
     return 0
 
 
+def run_probe(args):
+    """Per-kernel timing of one plan on a random medium (kernel studies and ncu
+    captures of a chosen geometry): --probe N0xN1xN2 --probe-split S0xS1xS2
+    [--probe-opts no_tma,force_tma,no_tune,corr_tf32]; 5 warm-up iterations,
+    then K iterations one by one with CUDA events per kernel and K graph-replayed."""
+    import torch
+
+    import paper_2410_02395_gb300 as pkg
+
+    shape = tuple(int(v) for v in args.probe.split("x"))
+    split = tuple(int(v) for v in args.probe_split.split("x"))
+    opts = {k: True for k in args.probe_opts.split(",") if k}
+    g = torch.Generator(device="cuda").manual_seed(1)
+    n = (1.0 + 0.5 * torch.rand(shape, generator=g, device="cuda")).to(torch.complex64)
+    src = torch.zeros(shape, dtype=torch.complex64, device="cuda")
+    src[tuple(v // 2 for v in shape)] = 1.0
+    plan = pkg.Plan(shape, 0.25, 1.0, n, boundary_widths=((8, 8),) * 3, split=split, truncation=8, **opts)
+    plan.set_source(src)
+    plan.iterate(5, 0.0, no_poll=True)
+    K = max(1, args.steps)
+    prof = plan.profile(K)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    plan.iterate(K, 0.0, no_poll=True)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / K
+    info = plan.info()
+    print(json.dumps({"probe": list(shape), "split": list(split), "opts": sorted(opts), "ms_per_iter": ms,
+                      "voxel_iterations_per_s": shape[0] * shape[1] * shape[2] / ms * 1e3,
+                      "tuning": info["tuning"], "tma_groups": info["tma_groups"],
+                      "kernels_ms_per_iter": {k: v[1] / K for k, v in prof.items()}}), flush=True)
+    plan.close()
+    return 0
+
+
 def timed_iterations(plan, K, warmup, stream, dev, ws, torch, clocks=None):
     """CUDA-event milliseconds of K iterations (graph replays, no polling) after warm-up,
     max over ranks."""
@@ -398,6 +437,35 @@ def cufft_comparison(torch, dev, info, prof, K, reps=5):
                    "global grid and fuse the medium, source, corrections and update" % reps}
 
 
+def activation_comparison(pkg, torch, dev, shape=(1024, 128, 128), split=(8, 1, 1), tol=1e-4, max_iter=40000):
+    """Subdomain activation (Sec. 3.1): time to tolerance with and without it on a
+    long domain (256 wavelengths along axis 0 at lambda/4, 8 subdomains of 128^3,
+    the C2 sphere recipe, 8-px layers, t = 8) with the point source in the first
+    subdomain, far from the others. Both solves are timed from mbs_set_source to
+    the stop (x form, FP32 corrections)."""
+    from synth import point_source, spheres_medium
+
+    n = spheres_medium(shape, count=40, r_range=(4, 20), n_range=(1.0, 1.6), seed=106, margin=8)
+    src = point_source(shape, (64, shape[1] // 2, shape[2] // 2))
+    n_dev = torch.from_numpy(n).to(dev)
+    s_dev = torch.from_numpy(src).to(dev)
+    out = {"workload": "%s grid, split %s, t=8, 40 spheres, 8-px layers, point source at (64, %d, %d)" % (
+        "x".join(map(str, shape)), "x".join(map(str, split)), shape[1] // 2, shape[2] // 2), "tol": tol}
+    for name, kw in (("without", {}), ("with", {"activation": True})):
+        p = pkg.Plan(shape, 0.25, 1.0, n_dev, boundary_widths=((8, 8),) * 3, split=split, truncation=8, **kw)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        p.set_source(s_dev)
+        st, it, eps = p.iterate(max_iter, tol)
+        torch.cuda.synchronize(dev)
+        out[name] = {"status": st, "iterations": it, "residual": eps, "seconds": time.perf_counter() - t0}
+        p.close()
+    out["speedup"] = out["without"]["seconds"] / out["with"]["seconds"]
+    del n_dev, s_dev
+    torch.cuda.empty_cache()
+    return out
+
+
 def workload_values(pkg, torch, dev, names, steps, warmup, ws):
     """Device-timed value (and the mixed form's) of other single-grid workloads."""
     import numpy as np
@@ -450,6 +518,7 @@ def run_batch(args, pkg, torch, ws, rank, dev):
     K = max(G, (args.steps // 10 // G) * G)
     b = pkg.Batch(plans, stream=stream.cuda_stream, graph_iters=G)
     b.iterate(max(args.warmup, 3), 0.0, no_poll=True)
+    n_launch, fused = b.launches_per_iteration()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(dev.index)
     torch.cuda.synchronize(dev)
@@ -501,6 +570,10 @@ def run_batch(args, pkg, torch, ws, rank, dev):
                            "l2": "no flush: %.0f MB per field summed over the solves (> 129 MB L2)" % (vox * 8 / 1e6),
                            "parallelism": "replicas" if ws > 1 else "single GPU", "graph_iters": G},
                 "clocks": clk,
+                "gpu_launches": n_launch * K,
+                "batch": {"fused": fused, "launches_per_iteration": n_launch,
+                          "how": "one launch per pass and subdomain edge over all solves" if fused else
+                                 "one graph of every solve's own launches on forked streams"},
                 "sequential": {"value": vox * K / seq, "unit": UNIT,
                                "how": "the same 64 solves one after another, each with its own graph replays"},
                 "time_to_tol": ttt}
@@ -520,20 +593,27 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-error", action="store_true", help="skip the error-vs-oracle leg")
     ap.add_argument("--no-extra", action="store_true", help="skip the other single-grid workloads (C2, C3)")
+    ap.add_argument("--no-activation", action="store_true", help="skip the subdomain-activation comparison")
     ap.add_argument("--ttt", action="store_true", help="run the time-to-tolerance leg (long at 1280^3)")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance leg of C4")
     ap.add_argument("--ttt-max-iter", type=int, default=40000)
+    ap.add_argument("--ttt-history", default="", help="file (.npy) for the residual history of the --ttt leg")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_TEXT),
                     help="benchmark workload (default: the 1280^3 configuration C5)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 3xTF32-correction timing")
     ap.add_argument("--t-sweep", default="", help="comma-separated truncation widths: ms per iteration for each "
                     "on the same workload (Sec. 4.2.1, Fig. 7c)")
+    ap.add_argument("--probe", default="", help="per-kernel timing of one plan of this grid (N0xN1xN2)")
+    ap.add_argument("--probe-split", default="1x1x1")
+    ap.add_argument("--probe-opts", default="", help="comma-separated Plan flags, e.g. no_tma,force_tma")
     ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-shape", default="128x128x128", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-iters", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_child:
         return cpu_child(args)
+    if args.probe:
+        return run_probe(args)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -655,8 +735,24 @@ def main():
             pr.set_source(src_dev)
             st_tol, it_tol, eps_tol = pr.iterate(args.ttt_max_iter, params["tol"])
             torch.cuda.synchronize(dev)
+            secs = time.perf_counter() - t0
             ttt_line = {"tol": params["tol"], "status": st_tol, "iterations": it_tol, "residual": eps_tol,
-                        "seconds": time.perf_counter() - t0, "form": "residual form, FP32 corrections"}
+                        "seconds": secs, "form": "residual form, FP32 corrections"}
+            hist = pr.history(it_tol)
+            if args.ttt_history:
+                np.save(args.ttt_history, hist)
+            if st_tol != "MBS_OK" and len(hist) >= 200:
+                # extrapolation from the residual's slope over the last half of the run (log eps linear in n)
+                h = np.log(np.maximum(hist, 1e-300))
+                k = np.arange(len(h))
+                half = len(h) // 2
+                slope, icpt = np.polyfit(k[half:], h[half:], 1)
+                if slope < 0:
+                    n_tol = int(np.ceil((np.log(params["tol"]) - icpt) / slope))
+                    ttt_line["extrapolated"] = {
+                        "iterations": n_tol, "seconds": secs / it_tol * n_tol,
+                        "how": "log eps fitted linearly over iterations %d-%d (slope %.3e per iteration); an "
+                               "extrapolation, not a measurement" % (half, len(h) - 1, slope)}
             pr.close()
 
         # ---- truncation sweep: iteration time against t ------------------------
@@ -681,6 +777,9 @@ def main():
     extra = None
     if not args.no_extra and args.workload == "C5":
         extra = workload_values(pkg, torch, dev, ["C2", "C3"], args.steps, args.warmup, ws)
+    activation = None
+    if rank == 0 and not args.no_activation and args.workload == "C5":
+        activation = activation_comparison(pkg, torch, dev)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
@@ -709,6 +808,7 @@ def main():
             "no_graph": no_graph,
             "error": error,
             "workloads": extra,
+            "activation": activation,
             "time_to_tol": ttt_line,
         }
         if args.t_sweep:

@@ -99,14 +99,15 @@ typedef enum mbs_operator {
                                         arithmetic; in complex64 the residual has no floor set by ||x||,
                                         so tolerances below that floor are reachable. Costs about
                                         24 B per voxel and iteration more (x and its low word).      */
-#define MBS_FLAG_NO_TMA (1u << 3) /* feed the axis-1 and axis-0 FFT passes with per-thread global
-                                     loads instead of tensor-map (TMA) copies into double-buffered
-                                     shared memory. Default: TMA where the edge has TMA kernels
-                                     (32, 64, 128, 256, 320), the grid's row pitch is a multiple of
-                                     16 bytes and the plan-time timing finds TMA faster.          */
-#define MBS_FLAG_FORCE_TMA (1u << 4) /* keep every tensor-map feed the plan can build instead of timing
-                                     the TMA-fed against the register-fed pass at plan creation and
-                                     keeping the faster (results are identical)                   */
+#define MBS_FLAG_NO_TMA (1u << 3) /* feed the axis-1 FFT passes with per-thread global loads instead
+                                     of tensor-map (TMA) copies into double-buffered shared memory.
+                                     Default: TMA where the edge has TMA kernels (32, 64, 128, 256,
+                                     320), the grid's row pitch is a multiple of 16 bytes and the
+                                     plan-time timing finds TMA faster.                           */
+#define MBS_FLAG_FORCE_TMA (1u << 4) /* keep every tensor-map feed the plan can build, without the
+                                     plan-time timing, and feed the axis-0 pass (forward transform,
+                                     propagator, inverse) by TMA too, which only this flag does
+                                     (results are identical)                                      */
 #define MBS_FLAG_PLAIN_STEPS (1u << 5) /* comparison form of the iteration: every step of
                                      Eq. wavesim_iter is its own launch over the whole grid (E x,
                                      u = B x + y - E x, three forward FFT passes, the propagator,
@@ -115,6 +116,29 @@ typedef enum mbs_operator {
                                      and the residual summed and the stop test taken on the host
                                      after every iteration. Same iterates as the default form up to
                                      FP32 rounding; not with MBS_FLAG_RESIDUAL_FORM or in batches. */
+#define MBS_FLAG_ACTIVATION (1u << 6) /* subdomain activation (Sec. 3.1, "Implementation"): after
+                                     mbs_set_source only the subdomains that meet the bounding box of
+                                     the source's non-zero voxels are computed; every graph_iters
+                                     iterations an inactive subdomain next to an active one is
+                                     activated once the norm of the field that neighbour transfers
+                                     into its boundary layers exceeds activation_threshold *
+                                     ||r_0||. The inactive subdomains keep x = 0 and add nothing to
+                                     the residual, so the early iterates differ slightly from the
+                                     unmasked ones; the iteration converges to the same solution
+                                     (it converges from any start). mbs_iterate polls the device
+                                     between replays while any subdomain is inactive, no_poll or
+                                     not. The default (x) form only; needs t > 0, mixed-radix axis-2
+                                     edges and 2 t S_2 <= 64; not in batches. A warm start
+                                     (mbs_set_initial_field) activates every subdomain.          */
+#define MBS_FLAG_NO_TUNE (1u << 7) /* skip the plan-time tuner (see mbs_plan_info.tuning) and its
+                                     on-disk cache: TMA feed wherever a tensor map exists, with as
+                                     many CTAs per SM as fit, and side-split correction kernels of
+                                     128 threads. The tuner only chooses launch shapes, so tuned and
+                                     untuned plans give bit-identical iterates. The cache file is
+                                     MBS_TUNE_CACHE if that environment variable is set (empty: no
+                                     cache), else $XDG_CACHE_HOME (or $HOME/.cache) /mbs_gb300/
+                                     tune-v1.txt, one line per (device, SM count, build, pass, edge,
+                                     grid) key.                                                   */
 
 typedef struct mbs_options {
   int32_t truncation;        /* t, the kept edge width (Sec. 3, Fig. 5); 0 -> 8 (Sec. 3.3);
@@ -135,6 +159,8 @@ typedef struct mbs_options {
                                 operators, in SM clock cycles; 0 -> about 2 s. Past it the call
                                 returns MBS_ETIMEOUT (a short bound lets a test provoke that path
                                 with copies that do complete)                                     */
+  double activation_threshold; /* MBS_FLAG_ACTIVATION: relative norm of the transferred field
+                                that activates a subdomain; 0 -> 1e-3                             */
 } mbs_options;
 
 /* Fill *opts with the defaults above. */
@@ -178,9 +204,13 @@ typedef struct mbs_plan_info {
   int64_t sizes[3][MBS_MAX_SPLIT];  /* subdomain edges along each axis                        */
   size_t device_bytes;       /* device memory held by the plan                                 */
   int32_t graph_iters;
-  int32_t tma_groups;        /* edge groups whose axis-1 pass or axis-0 (forward, multiplier,
-                                inverse) pass is fed by TMA (chosen at plan creation by timing
-                                both feeds; results are identical)                             */
+  int32_t tma_groups;        /* edge groups whose axis-1 pass (or, with MBS_FLAG_FORCE_TMA, axis-0
+                                pass) is fed by TMA (chosen at plan creation by timing both feeds;
+                                results are identical)                                          */
+  int32_t tune_source;       /* launch shapes: 0 defaults (MBS_FLAG_NO_TUNE, MBS_FLAG_FORCE_TMA or
+                                nothing to tune), 1 timed at plan creation, 2 from the cache     */
+  char tuning[256];          /* the choices, e.g. "axis1/320:tmax1 corr01:side/128" (axis-1 pass
+                                of edge 320 TMA-fed with one CTA per SM)                        */
 } mbs_plan_info;
 
 MBS_API mbs_status mbs_plan_get_info(const mbs_plan *plan, mbs_plan_info *info);
@@ -224,6 +254,14 @@ MBS_API mbs_status mbs_set_initial_field(mbs_plan *plan, const void *x0);
  */
 MBS_API mbs_status mbs_iterate(mbs_plan *plan, int32_t n_iter, double tol, int32_t no_poll, int32_t *iters_done,
                        double *residual);
+
+/*
+ * Subdomain activation state (MBS_FLAG_ACTIVATION): flags[s] = 1 if subdomain s
+ * is computed, s = (j0 * split[1] + j1) * split[2] + j2, for s < cap (flags
+ * nullable); *n_active (nullable) receives the number of active subdomains.
+ * Without the flag every subdomain is active.
+ */
+MBS_API mbs_status mbs_get_active_subdomains(const mbs_plan *plan, int32_t *flags, int32_t cap, int32_t *n_active);
 
 /* Copy the current field x (complex64, shape) to out (host or device). */
 MBS_API mbs_status mbs_get_field(const mbs_plan *plan, void *out);
@@ -302,6 +340,16 @@ MBS_API mbs_status mbs_batch_create(mbs_batch **batch, int32_t nplans, mbs_plan 
  */
 MBS_API mbs_status mbs_batch_iterate(mbs_batch *batch, int32_t n_iter, double tol, int32_t no_poll, int32_t *iters,
                                      double *residuals, int32_t *statuses);
+/*
+ * Kernel launches per iteration of the whole batch (-1 on error); *fused
+ * (nullable) is 1 when the batch runs in its fused form: one launch per pass
+ * and subdomain edge over all plans (grid.z selecting the plan), which applies
+ * when every plan iterates in the default x form with FP32 corrections, every
+ * subdomain edge is a mixed-radix length of at most 128 (and at least 2t on
+ * corrected axes 0 and 1) and all plans share t; otherwise the batch graph
+ * holds every plan's own launches.
+ */
+MBS_API int32_t mbs_batch_launches_per_iteration(mbs_batch *batch, int32_t *fused);
 MBS_API void mbs_batch_destroy(mbs_batch *batch);
 
 MBS_API void mbs_plan_destroy(mbs_plan *plan);

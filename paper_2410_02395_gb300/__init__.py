@@ -37,7 +37,8 @@ class _Options(C.Structure):
     _fields_ = [("truncation", C.c_int32), ("alpha", C.c_double), ("periodic_mask", C.c_uint32),
                 ("absorb_kappa", C.c_double), ("split_sizes", C.POINTER(C.c_int64)), ("flags", C.c_uint32),
                 ("graph_iters", C.c_int32), ("stream", C.c_void_p), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t), ("tma_wait_cycles", C.c_int64)]
+                ("workspace_bytes", C.c_size_t), ("tma_wait_cycles", C.c_int64),
+                ("activation_threshold", C.c_double)]
 
 
 class _Info(C.Structure):
@@ -45,7 +46,7 @@ class _Info(C.Structure):
                 ("contrast", C.c_double), ("block_norm", C.c_double), ("a", C.c_int32 * 3), ("t", C.c_int32),
                 ("alpha", C.c_double), ("shape", C.c_int64 * 3), ("split", C.c_int32 * 3),
                 ("sizes", (C.c_int64 * MAX_SPLIT) * 3), ("device_bytes", C.c_size_t), ("graph_iters", C.c_int32),
-                ("tma_groups", C.c_int32)]
+                ("tma_groups", C.c_int32), ("tune_source", C.c_int32), ("tuning", C.c_char * 256)]
 
 
 _lib = None
@@ -79,6 +80,7 @@ def load_library(path=None):
     lib.mbs_set_initial_field.argtypes = [vp, vp]
     lib.mbs_iterate.argtypes = [vp, i32, dbl, i32, C.POINTER(i32), C.POINTER(dbl)]
     lib.mbs_get_field.argtypes = [vp, vp]
+    lib.mbs_get_active_subdomains.argtypes = [vp, C.POINTER(i32), i32, C.POINTER(i32)]
     lib.mbs_get_history.argtypes = [vp, C.POINTER(dbl), i32, C.POINTER(i32)]
     lib.mbs_solve.argtypes = [vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), C.POINTER(dbl)]
     lib.mbs_profile_iterations.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(dbl)]
@@ -86,6 +88,8 @@ def load_library(path=None):
     lib.mbs_kernel_kind_name.restype = C.c_char_p
     lib.mbs_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), vp, i32]
     lib.mbs_batch_iterate.argtypes = [vp, i32, dbl, i32, C.POINTER(i32), C.POINTER(dbl), C.POINTER(i32)]
+    lib.mbs_batch_launches_per_iteration.argtypes = [vp, C.POINTER(i32)]
+    lib.mbs_batch_launches_per_iteration.restype = C.c_int32
     lib.mbs_batch_destroy.argtypes = [vp]
     lib.mbs_batch_destroy.restype = None
     lib.mbs_plan_destroy.argtypes = [vp]
@@ -93,7 +97,7 @@ def load_library(path=None):
     lib.mbs_last_error.argtypes = []
     lib.mbs_last_error.restype = C.c_char_p
     for name in ("mbs_plan_create", "mbs_workspace_bytes", "mbs_plan_get_info", "mbs_apply_operator",
-                 "mbs_set_source", "mbs_set_initial_field", "mbs_iterate", "mbs_get_field", "mbs_get_history", "mbs_solve",
+                 "mbs_set_source", "mbs_set_initial_field", "mbs_get_active_subdomains", "mbs_iterate", "mbs_get_field", "mbs_get_history", "mbs_solve",
                  "mbs_profile_iterations", "mbs_batch_create", "mbs_batch_iterate"):
         getattr(lib, name).restype = C.c_int
     if path is None:
@@ -161,7 +165,9 @@ class Plan:
     def __init__(self, shape, pixel_size, wavelength, refractive_index, boundary_widths=((0, 0),) * 3,
                  split=(1, 1, 1), truncation=8, alpha=0.75, periodic=(False, False, False), kappa=0.5,
                  split_sizes=None, graph_iters=0, no_graph=False, corr_tf32=False, residual_form=False,
-                 no_tma=False, force_tma=False, plain_steps=False, tma_wait_cycles=0, stream=None, workspace=None):
+                 no_tma=False, force_tma=False, plain_steps=False, activation=False, activation_threshold=0.0,
+                 no_tune=False,
+                 tma_wait_cycles=0, stream=None, workspace=None):
         self.lib = load_library()
         self.shape = tuple(int(s) for s in shape)
         opts = _Options()
@@ -172,8 +178,10 @@ class Plan:
         opts.absorb_kappa = float(kappa)
         opts.graph_iters = int(graph_iters)
         opts.flags = (1 if no_graph else 0) | (2 if corr_tf32 else 0) | (4 if residual_form else 0) | \
-            (8 if no_tma else 0) | (16 if force_tma else 0) | (32 if plain_steps else 0)
+            (8 if no_tma else 0) | (16 if force_tma else 0) | (32 if plain_steps else 0) | (64 if activation else 0) | \
+            (128 if no_tune else 0)
         opts.tma_wait_cycles = int(tma_wait_cycles)
+        opts.activation_threshold = float(activation_threshold)
         self._split_sizes = None
         if split_sizes is not None:
             flat = [int(v) for d in range(3) for v in split_sizes[d]]
@@ -203,7 +211,8 @@ class Plan:
                     block_norm=inf.block_norm, a=list(inf.a), t=inf.t, alpha=inf.alpha, shape=tuple(inf.shape),
                     split=tuple(inf.split),
                     sizes=[list(inf.sizes[d][:inf.split[d]]) for d in range(3)], device_bytes=inf.device_bytes,
-                    graph_iters=inf.graph_iters, tma_groups=inf.tma_groups)
+                    graph_iters=inf.graph_iters, tma_groups=inf.tma_groups, tune_source=inf.tune_source,
+                    tuning=inf.tuning.decode())
 
     @staticmethod
     def workspace_bytes(shape, split, truncation=8, split_sizes=None, residual_form=False):
@@ -262,6 +271,15 @@ class Plan:
                                   C.byref(res))
         _check(self.lib, st, ok=(0, 4))
         return STATUS[st], it.value, res.value
+
+    def active_subdomains(self):
+        """Activation flags of the subdomains, shape split (all 1 without activation)."""
+        sp = self.info()["split"]
+        nsub = sp[0] * sp[1] * sp[2]
+        flags = (C.c_int32 * nsub)()
+        na = C.c_int32()
+        _check(self.lib, self.lib.mbs_get_active_subdomains(self.handle, flags, nsub, C.byref(na)))
+        return np.array(flags[:], dtype=np.int32).reshape(sp)
 
     def field(self, out=None, like=None):
         out = self._out(out, like)
@@ -337,6 +355,14 @@ class Batch:
         _check(self.lib, self.lib.mbs_batch_iterate(self.handle, int(n_iter), float(tol), 1 if no_poll else 0,
                                                     it, res, sts), ok=(0, 4))
         return [(STATUS[sts[i]], it[i], res[i]) for i in range(n)]
+
+    def launches_per_iteration(self):
+        """(kernel launches per iteration of the whole batch, fused form or not)."""
+        fused = C.c_int32()
+        n = self.lib.mbs_batch_launches_per_iteration(self.handle, C.byref(fused))
+        if n < 0:
+            raise MBSError(3, self.lib.mbs_last_error().decode())
+        return n, bool(fused.value)
 
     def close(self):
         if getattr(self, "handle", None):

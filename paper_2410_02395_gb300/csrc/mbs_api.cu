@@ -6,15 +6,32 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdlib.h>
+#include <sys/stat.h>
+
 #include <algorithm>
+#include <fstream>
+#include <functional>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/mbs.h"
 #include "mbs_internal.h"
 
 using namespace mbs;
+
+namespace {
+// NVTX range over a C-ABI call (visible in Nsight timelines; header-only NVTX 3,
+// a no-op when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 namespace {
 
@@ -143,6 +160,12 @@ struct mbs_plan {
   bool bl_axis2;  // an axis-2 edge is a Bluestein length (no fused axis-2 corrections then)
   // tensor maps of the TMA-fed passes, keyed by axis * 65536 + edge
   std::map<int, CUtensorMap> tmaps;
+  // tuner's choices (see tune_plan): CTAs per SM of the TMA-fed axis-1 pass per
+  // edge (0: as many as fit), correction kernel shape
+  std::map<int, int> tma_ctas;
+  int corr_variant, corr_block;
+  int tune_source;       // 0 defaults, 1 timed at creation, 2 read from the cache
+  std::string tuning;
   double* partials;
   int n_rows_partials, n_shell_partials;
   DevState* state;
@@ -157,6 +180,13 @@ struct mbs_plan {
   int64_t sbox[6];
   bool have_source;
   unsigned source_gen;  // incremented by every mbs_set_source (batches capture again)
+  // subdomain activation (MBS_FLAG_ACTIVATION)
+  int* act_dev;             // flag per subdomain, (j0 S1 + j1) S2 + j2
+  double* act_norms;        // per subdomain: squared norm of the transferred field
+  ActFace* act_faces;       // faces checked by one activation step (at most 6 per subdomain)
+  std::vector<int> act_host;
+  bool act_on;              // some subdomain is inactive: the iteration masks its kernels
+  double act_thr;           // activate when the transferred norm exceeds act_thr * ||r_0||
   // graph
   cudaGraphExec_t graph;
   bool graph_ready;
@@ -234,6 +264,11 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
   char* pfst = take(sizeof(DevState));
   char* phist = take(kHistCap * sizeof(double));
   char* pbox = take(6 * sizeof(int));
+  const int nsub = p->S[0] * p->S[1] * p->S[2];
+  const bool act = (p->flags & MBS_FLAG_ACTIVATION) != 0;
+  char* pact = act ? take(nsub * sizeof(int)) : nullptr;
+  char* pactn = act ? take(nsub * sizeof(double)) : nullptr;
+  char* pactf = act ? take(6 * nsub * sizeof(ActFace)) : nullptr;
   if (assign) {
     p->x = (float2*)px;
     p->B = (float2*)pB;
@@ -270,6 +305,9 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
     p->free_state = (DevState*)pfst;
     p->history = (double*)phist;
     p->box_dev = (int*)pbox;
+    p->act_dev = (int*)pact;
+    p->act_norms = (double*)pactn;
+    p->act_faces = (ActFace*)pactf;
   }
   return off;
 }
@@ -295,6 +333,10 @@ mbs_status validate_and_fill(mbs_plan* p, const int64_t shape[3], double h, doub
   if (o && o->tma_wait_cycles < 0) return fail(MBS_EINVAL, "tma_wait_cycles must be >= 0");
   if ((p->flags & MBS_FLAG_PLAIN_STEPS) && (p->flags & MBS_FLAG_RESIDUAL_FORM))
     return fail(MBS_EINVAL, "the plain-step form has no residual form");
+  if ((p->flags & MBS_FLAG_ACTIVATION) && (p->flags & (MBS_FLAG_RESIDUAL_FORM | MBS_FLAG_PLAIN_STEPS)))
+    return fail(MBS_EINVAL, "subdomain activation is for the default (x) form of the iteration");
+  if (o && o->activation_threshold < 0.0) return fail(MBS_EINVAL, "activation_threshold must be >= 0");
+  p->act_thr = (o && o->activation_threshold > 0.0) ? o->activation_threshold : 1e-3;
   p->tma_wait = o ? (long long)o->tma_wait_cycles : 0;
   int k = 0;
   for (int d = 0; d < 3; d++) {
@@ -628,6 +670,8 @@ cudaError_t run_corr_rec(mbs_plan* p, const float2* F, float2* C, const DevState
   c.tb = p->tb;
   c.g = p->g;
   c.state = state;
+  c.variant = p->corr_variant;
+  c.block = p->corr_block;
   for (int d = 0; d < (axis2 ? 3 : 2); d++) {
     if (!(p->t > 0 && p->a[d] > 0)) continue;
     c.axis = d;
@@ -647,15 +691,23 @@ cudaError_t run_corr(mbs_plan* p, const float2* F, float2* C, const DevState* st
 // it, register-fed otherwise.
 cudaError_t strided_pass(const mbs_plan* p, const PassArgs& a, int n, bool inv) {
   auto it = p->tmaps.find(1 * 65536 + n);
-  if (it != p->tmaps.end()) return launch_strided_tma(n, 1, inv, a, it->second, p->stream);
+  if (it != p->tmaps.end()) {
+    PassArgs b = a;
+    auto c = p->tma_ctas.find(n);
+    b.tma_ctas = c == p->tma_ctas.end() ? 0 : c->second;
+    return launch_strided_tma(n, 1, inv, b, it->second, p->stream);
+  }
   return launch_strided(n, 1, inv, a, p->stream);
 }
 
 // Axis-0 pass of one edge group (a.mode: MID_PROP, MID_LSYM, MID_FWD, MID_INV):
-// the forward-multiplier-inverse modes are TMA-fed where the plan kept a tensor
-// map for the edge (at 128 the register-fed kernel at four CTAs per SM is
-// issue-bound and faster, 76.1 against 78.9 us on the 256^3 workload; at 320,
-// one CTA per SM, the prefetching feed pays).
+// the forward-multiplier-inverse modes are TMA-fed only where the plan holds an
+// axis-0 tensor map, which it builds with MBS_FLAG_FORCE_TMA alone: this pass
+// does two transforms per tile and is issue-bound, and the register-fed kernel
+// was faster inside the iteration at every edge measured (128: 76.1 against
+// 78.9 us on the 256^3 workload; 320: 11.7 against 12.6 ms on the 1280^3 one),
+// although isolated back-to-back launches at plan creation sometimes timed the
+// TMA form faster.
 cudaError_t mid_pass(const mbs_plan* p, const PassArgs& a, int n) {
   if (a.mode == MID_PROP || a.mode == MID_LSYM) {
     auto it = p->tmaps.find(0 * 65536 + n);
@@ -664,57 +716,212 @@ cudaError_t mid_pass(const mbs_plan* p, const PassArgs& a, int n) {
   return launch_mid(n, a, p->stream);
 }
 
-// Plan-time choice between the TMA-fed and the register-fed axis-1 and axis-0
-// passes of each edge group: both forms run the same arithmetic (bit-identical
-// results), so the plan times both on its own geometry (axis 1 forward and
-// inverse, axis 0 with the propagator; CUDA events on the plan's stream; the
-// FFT buffer's contents do not matter): 2 warm-up launches of each form, then
-// three rounds that alternate the forms, 3 launches per form and round, the
-// fastest round of each form counting; the tensor map is kept only where TMA
-// is faster.
-mbs_status autotune_strided(mbs_plan* p) {
-  if (p->tmaps.empty() || (p->flags & MBS_FLAG_FORCE_TMA)) return MBS_OK;
+// ---------------------------------------------------------------------------
+// Plan-time tuner. Every choice below only changes how a pass is launched, not
+// its arithmetic, so tuned and untuned plans give bit-identical iterates:
+//  - the axis-1 pass of each edge group: register-fed, or TMA-fed with 1 .. m
+//    resident CTAs per SM (m: as many as fit);
+//  - the FP32 axis-0/1 edge-correction kernels: one thread per (pencil,
+//    subdomain, side) or per (pencil, subdomain), 64 or 128 threads per block.
+// Each candidate is timed on the plan's own buffers (CUDA events on the plan's
+// stream; the contents of the FFT buffer do not matter): one warm-up launch of
+// every candidate, then three rounds that alternate the candidates, three
+// launches per candidate and round, the fastest round counting. The choice is
+// kept in an on-disk cache keyed by the device, its SM count, the library
+// build, the pass, the edge and the grid (MBS_TUNE_CACHE names the file, empty
+// disables it; default $XDG_CACHE_HOME or $HOME/.cache, mbs_gb300/tune-v1.txt),
+// so later plans of the same geometry skip the timing. MBS_FLAG_NO_TUNE keeps
+// the defaults: TMA feed wherever a tensor map exists with as many CTAs as fit,
+// side-split correction kernels of 128 threads.
+// ---------------------------------------------------------------------------
+const char* kTuneBuild = "tune-v2 " __DATE__ " " __TIME__;
+
+std::string tune_cache_path() {
+  const char* e = getenv("MBS_TUNE_CACHE");
+  if (e) return std::string(e);
+  const char* x = getenv("XDG_CACHE_HOME");
+  const char* h = getenv("HOME");
+  std::string base = (x && *x) ? std::string(x) : (h && *h ? std::string(h) + "/.cache" : std::string());
+  if (base.empty()) return std::string();
+  return base + "/mbs_gb300/tune-v1.txt";
+}
+
+std::mutex g_tune_mu;
+
+// The cached value of key, or "" (the file is read at every lookup: plans are few).
+std::string tune_cache_get(const std::string& path, const std::string& key) {
+  if (path.empty()) return std::string();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::ifstream in(path);
+  std::string line, val;
+  while (std::getline(in, line)) {
+    const size_t tab = line.find('\t');
+    if (tab != std::string::npos && line.compare(0, tab, key) == 0 && tab == key.size()) val = line.substr(tab + 1);
+  }
+  return val;
+}
+
+void tune_cache_put(const std::string& path, const std::string& key, const std::string& val) {
+  if (path.empty()) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos && slash > 0) {  // mkdir -p of the parent directory
+    const std::string dir = path.substr(0, slash);
+    for (size_t k = 1; k <= dir.size(); k++)
+      if (k == dir.size() || dir[k] == '/') mkdir(dir.substr(0, k).c_str(), 0755);
+  }
+  std::ofstream out(path, std::ios::app);
+  if (out) out << key << '\t' << val << '\n';
+}
+
+std::string tune_key(const mbs_plan* p, const char* kind, int n) {
+  cudaDeviceProp prop;
+  int sms = 0;
+  std::string name = "gpu";
+  if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) {
+    name = prop.name;
+    sms = prop.multiProcessorCount;
+  } else {
+    cudaGetLastError();
+  }
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s|sm%d|%s|%s|n%d|%lldx%lldx%lld|s%dx%dx%d|t%d", name.c_str(), sms, kTuneBuild, kind, n,
+           (long long)p->N[0], (long long)p->N[1], (long long)p->N[2], p->S[0], p->S[1], p->S[2], p->t);
+  return std::string(buf);
+}
+
+// Fastest of `count` candidates: a warm-up launch of each, then three rounds
+// alternating the candidates, three timed launches per candidate and round,
+// the fastest round counting. Before every timed launch the L2 is flushed by
+// writing `flush` (256 MB, if given): inside the iteration a pass finds its
+// data in HBM, while back-to-back launches on a grid of about the L2's size
+// would find much of it cached and favour the wrong shape.
+constexpr long long kFlushElems = 32ll << 20;  // float2: 256 MB
+mbs_status time_candidates(mbs_plan* p, int count, const std::function<cudaError_t(int)>& launch, float2* flush,
+                           int* best_out) {
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
+  std::vector<float> best(count, 1e30f);
+  mbs_status st = MBS_OK;
+  for (int v = 0; v < count && !st; v++)
+    if (launch(v)) st = fail(MBS_ECUDA, "tuning launch failed");
+  for (int round = 0; round < 3 && !st; round++)
+    for (int v = 0; v < count && !st; v++) {
+      float tot = 0.f;
+      for (int r = 0; r < 3 && !st; r++) {
+        float ms = 0.f;
+        if (flush && launch_zero(flush, kFlushElems, p->stream)) st = fail(MBS_ECUDA, "tuning flush failed");
+        if (!st && cudaEventRecord(e0, p->stream)) st = fail(MBS_ECUDA, "tuning event failed");
+        if (!st && launch(v)) st = fail(MBS_ECUDA, "tuning launch failed");
+        if (!st && (cudaEventRecord(e1, p->stream) || cudaEventSynchronize(e1) || cudaEventElapsedTime(&ms, e0, e1)))
+          st = fail(MBS_ECUDA, "tuning event failed");
+        tot += ms;
+      }
+      if (!st) best[v] = std::min(best[v], tot);
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  *best_out = (int)(std::min_element(best.begin(), best.end()) - best.begin());
+  return MBS_OK;
+}
+
+mbs_status tune_plan_with(mbs_plan* p, float2* flush);
+
+mbs_status tune_plan(mbs_plan* p) {
+  NvtxRange nvtx_("mbs tuner");
+  float2* flush = nullptr;  // released again below; without it the timing runs unflushed
+  if (cudaMalloc((void**)&flush, kFlushElems * sizeof(float2)) != cudaSuccess) {
+    cudaGetLastError();
+    flush = nullptr;
+  }
+  const mbs_status st = tune_plan_with(p, flush);
+  if (flush) cudaFree(flush);
+  return st;
+}
+
+mbs_status tune_plan_with(mbs_plan* p, float2* flush) {
+  const bool fixed = (p->flags & (MBS_FLAG_NO_TUNE | MBS_FLAG_FORCE_TMA)) != 0;
+  const std::string path = tune_cache_path();
+  int timed = 0, cached = 0;
+  std::string summary;
   PassArgs a = base_args(p);
   a.state = p->free_state;
   a.tma_wait = 0;  // the full bound: a caller's short bound is for the iteration and the operators
+  a.mode = MID_PROP;
+  // axis-1 passes: candidate 0 register-fed, c >= 1 TMA-fed with c CTAs per SM
   std::vector<int> drop;
-  for (int axis = 0; axis < 2; axis++) {
-    for (auto& gy : p->groups[axis]) {
-      auto it = p->tmaps.find(axis * 65536 + gy.n);
-      if (it == p->tmaps.end()) continue;
-      a.nsub = gy.nsub;
-      memcpy(a.subs, gy.subs, sizeof(a.subs));
-      set_len_tables(p, a, gy.n);
-      a.mode = MID_PROP;
-      float best[2] = {1e30f, 1e30f};
-      auto launch = [&](int v, bool inv) -> cudaError_t {
-        if (axis == 0)
-          return v == 0 ? launch_mid_tma(gy.n, a, it->second, p->stream) : launch_mid(gy.n, a, p->stream);
-        return v == 0 ? launch_strided_tma(gy.n, 1, inv, a, it->second, p->stream)
-                      : launch_strided(gy.n, 1, inv, a, p->stream);
-      };
-      for (int v = 0; v < 2; v++)
-        if (launch(v, false) || launch(v, true)) return fail(MBS_ECUDA, "pass timing launch failed");
-      for (int round = 0; round < 3; round++)
-        for (int v = 0; v < 2; v++) {
-          CU(cudaEventRecord(e0, p->stream));
-          for (int r = 0; r < 3; r++)
-            if (launch(v, false) || launch(v, true)) return fail(MBS_ECUDA, "pass timing launch failed");
-          CU(cudaEventRecord(e1, p->stream));
-          CU(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          CU(cudaEventElapsedTime(&ms, e0, e1));
-          best[v] = std::min(best[v], ms);
-        }
-      if (best[1] < best[0]) drop.push_back(it->first);
+  for (auto& gy : p->groups[1]) {
+    auto it = p->tmaps.find(1 * 65536 + gy.n);
+    if (it == p->tmaps.end()) continue;
+    int choice = 0;  // TMA, as many CTAs as fit
+    if (!fixed) {
+      const std::string key = tune_key(p, "axis1", gy.n);
+      const std::string val = tune_cache_get(path, key);
+      if (!val.empty()) {
+        choice = atoi(val.c_str());
+        cached++;
+      } else {
+        const int m = std::max(1, tma_max_ctas(gy.n, 2));
+        a.nsub = gy.nsub;
+        memcpy(a.subs, gy.subs, sizeof(a.subs));
+        set_len_tables(p, a, gy.n);
+        int best = 0;
+        mbs_status st = time_candidates(p, m + 1, [&](int v) -> cudaError_t {
+          if (v == 0) {
+            cudaError_t e = launch_strided(gy.n, 1, false, a, p->stream);
+            return e ? e : launch_strided(gy.n, 1, true, a, p->stream);
+          }
+          PassArgs b = a;
+          b.tma_ctas = v;
+          cudaError_t e = launch_strided_tma(gy.n, 1, false, b, it->second, p->stream);
+          return e ? e : launch_strided_tma(gy.n, 1, true, b, it->second, p->stream);
+        }, flush, &best);
+        if (st) return st;
+        choice = best == 0 ? -1 : best;  // -1: register-fed
+        tune_cache_put(path, key, std::to_string(choice));
+        timed++;
+      }
     }
+    if (choice < 0) {
+      drop.push_back(it->first);
+    } else {
+      p->tma_ctas[gy.n] = choice;
+    }
+    summary += "axis1/" + std::to_string(gy.n) + ":" +
+               (choice < 0 ? std::string("reg") : "tma" + (choice > 0 ? "x" + std::to_string(choice) : std::string())) +
+               " ";
   }
   for (int k : drop) p->tmaps.erase(k);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  // FP32 correction kernels of axes 0 and 1 (both launches of the iteration's x corrections)
+  p->corr_variant = 0;
+  p->corr_block = 128;
+  const bool corr01 = p->has_shell && (p->a[0] > 0 || p->a[1] > 0) && !(p->flags & MBS_FLAG_CORR_TF32);
+  if (corr01 && !fixed) {
+    const std::string key = tune_key(p, "corr01", 0);
+    const std::string val = tune_cache_get(path, key);
+    int choice = 0;
+    if (!val.empty()) {
+      choice = atoi(val.c_str());
+      cached++;
+    } else {
+      mbs_status st = time_candidates(p, 4, [&](int v) -> cudaError_t {
+        p->corr_variant = v / 2;
+        p->corr_block = (v % 2) ? 64 : 128;
+        return run_corr(p, p->x, p->K, p->free_state, false);
+      }, flush, &choice);
+      if (st) return st;
+      tune_cache_put(path, key, std::to_string(choice));
+      timed++;
+    }
+    p->corr_variant = choice / 2;
+    p->corr_block = (choice % 2) ? 64 : 128;
+  }
+  if (corr01)
+    summary += std::string("corr01:") + (p->corr_variant ? "pencil" : "side") + "/" + std::to_string(p->corr_block);
+  p->tune_source = fixed ? 0 : (timed > 0 ? 1 : (cached > 0 ? 2 : 0));
+  p->tuning = summary;
   return MBS_OK;
 }
 
@@ -840,6 +1047,7 @@ cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
   a.X = p->x;
   a.Xout = p->x;
   a.state = p->state;
+  a.active = p->act_on ? p->act_dev : nullptr;  // subdomain activation: skip the inactive subdomains
   if (p->have_source) {
     a.S = p->src;
     for (int i = 0; i < 6; i++) a.sbox[i] = p->sbox[i];
@@ -858,6 +1066,7 @@ cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
     if (e) return e;
     ShellArgs s = shell_args(p);
     s.state = p->state;
+    s.active = a.active;
     s.mode = SHELL_UPDATE_ITER;
     s.partials = p->partials;
     s.slot0 = p->n_rows_partials;
@@ -991,6 +1200,94 @@ mbs_status iterate_plain(mbs_plan* p, int n_iter, double tol, DevState* out) {
   return MBS_OK;
 }
 
+// Subdomain activation (Sec. 3.1, "Implementation"): a subdomain starts active
+// only if it holds a source term; an inactive one next to an active neighbour
+// is activated once the norm of the field that neighbour transfers into its
+// boundary layers exceeds act_thr * ||r_n||, the current residual of the
+// active subdomains (relative to ||r_n|| rather than ||r_0||, so that a
+// transfer that stays small is still taken up once the active subdomains have
+// converged). Taken between graph replays (every graph_iters iterations) from
+// the current field; when every subdomain is active the masks are dropped and
+// the graph is captured again without them. `all` activates every subdomain
+// (the stop test fired while some were still inactive). *changed (nullable)
+// tells whether a flag changed.
+mbs_status activation_check(mbs_plan* p, const DevState& hs, bool all = false, bool* changed_out = nullptr) {
+  if (changed_out) *changed_out = false;
+  if (!p->act_on) return MBS_OK;
+  if (all) {
+    const int nsub = p->S[0] * p->S[1] * p->S[2];
+    p->act_host.assign(nsub, 1);
+    CU(cudaMemcpyAsync(p->act_dev, p->act_host.data(), nsub * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    p->act_on = false;
+    if (p->graph_ready) {
+      cudaGraphExecDestroy(p->graph);
+      p->graph_ready = false;
+    }
+    if (changed_out) *changed_out = true;
+    return MBS_OK;
+  }
+  if (hs.iter == 0 || !(hs.R0 > 0.0)) return MBS_OK;
+  NvtxRange nvtx_("mbs activation check");
+  const int S[3] = {p->S[0], p->S[1], p->S[2]};
+  const int nsub = S[0] * S[1] * S[2];
+  std::vector<ActFace> faces;
+  for (int sidx = 0; sidx < nsub; sidx++) {
+    if (p->act_host[sidx]) continue;
+    const int j[3] = {sidx / (S[1] * S[2]), (sidx / S[2]) % S[1], sidx % S[2]};
+    for (int d = 0; d < 3; d++) {
+      const AxisDesc& ax = p->g.ax[d];
+      for (int side = 0; side < 2; side++) {
+        const int jn = side == 0 ? ax.left[j[d]] : ax.right[j[d]];
+        if (jn < 0) continue;
+        int k[3] = {j[0], j[1], j[2]};
+        k[d] = jn;
+        const int nb = (k[0] * S[1] + k[1]) * S[2] + k[2];
+        if (p->act_host[nb]) faces.push_back(ActFace{sidx, nb, d, side == 0 ? 1 : 0});
+      }
+    }
+  }
+  if (faces.empty()) return MBS_OK;
+  std::vector<double> norms(nsub, 0.0);
+  CU(cudaMemcpyAsync(p->act_faces, faces.data(), faces.size() * sizeof(ActFace), cudaMemcpyHostToDevice, p->stream));
+  CU(cudaMemsetAsync(p->act_norms, 0, nsub * sizeof(double), p->stream));
+  CU(launch_act_norms(p->x, p->act_faces, (int)faces.size(), p->g, p->cW, p->act_norms, p->stream));
+  CU(cudaMemcpyAsync(norms.data(), p->act_norms, nsub * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  const double thr2 = p->act_thr * p->act_thr * hs.eps * hs.eps * hs.R0;  // (act_thr ||r_n||)^2
+  bool changed = false, every = true;
+  for (int sidx = 0; sidx < nsub; sidx++) {
+    if (!p->act_host[sidx] && norms[sidx] > thr2) {
+      p->act_host[sidx] = 1;
+      changed = true;
+    }
+    every = every && p->act_host[sidx];
+  }
+  if (changed_out) *changed_out = changed;
+  if (changed)
+    CU(cudaMemcpyAsync(p->act_dev, p->act_host.data(), nsub * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+  if (every) {
+    p->act_on = false;
+    if (p->graph_ready) {
+      CU(cudaStreamSynchronize(p->stream));
+      cudaGraphExecDestroy(p->graph);
+      p->graph_ready = false;
+    }
+  }
+  return MBS_OK;
+}
+
+// Every subdomain active (a warm start, or activation off).
+mbs_status activate_all(mbs_plan* p) {
+  if (!p->act_dev) return MBS_OK;
+  const int nsub = p->S[0] * p->S[1] * p->S[2];
+  p->act_host.assign(nsub, 1);
+  CU(cudaMemcpyAsync(p->act_dev, p->act_host.data(), nsub * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  p->act_on = false;
+  return MBS_OK;
+}
+
 mbs_status ensure_graph(mbs_plan* p) {
   if (p->graph_ready) return MBS_OK;
   cudaGraph_t g;
@@ -1094,6 +1391,7 @@ mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double p
                            const void* refractive_index, const int32_t boundary_widths[6], const int32_t split[3],
                            const mbs_options* opts) {
   g_err.clear();
+  NvtxRange nvtx_("mbs_plan_create");
   if (!plan_out || !refractive_index) return fail(MBS_EINVAL, "plan and refractive_index are required");
   *plan_out = nullptr;
   int ndev = 0;
@@ -1102,6 +1400,9 @@ mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double p
     return fail(MBS_ECUDA, "no CUDA device");
   }
   mbs_plan* p = new mbs_plan();
+  p->corr_variant = 0;
+  p->corr_block = 128;
+  p->tune_source = 0;
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     cudaGetLastError();
     delete p;
@@ -1123,6 +1424,16 @@ mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double p
   }
   build_groups(p);
   fill_grid_desc(p);
+  if (p->flags & MBS_FLAG_ACTIVATION) {
+    bool bl2 = false;
+    for (auto& gz : p->groups[2]) bl2 = bl2 || !fft_size_compiled(gz.n);
+    if (p->t == 0 || !shell_rows_supported(p->g) || bl2) {
+      delete p;
+      return fail(MBS_EUNSUPPORTED, "subdomain activation needs t > 0, the fused layer update (2 t S_2 <= 64) "
+                                    "and mixed-radix axis-2 edges");
+    }
+  }
+  p->act_on = false;
   if (p->graph_iters == 0) {
     const double v = (double)nvox(p);
     p->graph_iters = v >= 8e6 ? 10 : (v >= 1e6 ? 25 : 50);
@@ -1162,7 +1473,7 @@ mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double p
   st = upload_tables(p);
   if (st) return cleanup(st);
   if (!(p->flags & MBS_FLAG_NO_TMA)) {
-    for (int axis = 0; axis < 2; axis++)
+    for (int axis = (p->flags & MBS_FLAG_FORCE_TMA) ? 0 : 1; axis < 2; axis++)
       for (auto& gsz : p->groups[axis]) {
         CUtensorMap tm;
         if (gsz.n > 1 && make_tma_map(&tm, p->K, p->g, axis, gsz.n)) p->tmaps[axis * 65536 + gsz.n] = tm;
@@ -1185,7 +1496,7 @@ mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double p
   if (launch_state_arm(p->state, 0, 0.0, 1, kHistCap, p->stream) ||
       launch_state_arm(p->free_state, 0, 0.0, 1, kHistCap, p->stream))
     return cleanup(fail(MBS_ECUDA, "state init failed"));
-  st = autotune_strided(p);
+  st = tune_plan(p);
   if (st) return cleanup(st);
   // the allocation-free correction entry's scratch address on this device (its
   // first use would otherwise load the module that holds it); a failure here
@@ -1217,11 +1528,14 @@ mbs_status mbs_plan_get_info(const mbs_plan* p, mbs_plan_info* info) {
     for (int s = 0; s < p->S[d]; s++) info->sizes[d][s] = p->sizes[d][s];
   }
   info->tma_groups = (int32_t)p->tmaps.size();
+  info->tune_source = p->tune_source;
+  snprintf(info->tuning, sizeof(info->tuning), "%s", p->tuning.c_str());
   return MBS_OK;
 }
 
 mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* out) {
   g_err.clear();
+  NvtxRange nvtx_("mbs_apply_operator");
   if (!p || !x || !out) return fail(MBS_EINVAL, "null argument");
   if (x == out) return fail(MBS_EINVAL, "x and out must not alias");
   float2 *xd = nullptr, *od = nullptr;
@@ -1326,6 +1640,7 @@ mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* o
 
 mbs_status mbs_set_source(mbs_plan* p, const void* source) {
   g_err.clear();
+  NvtxRange nvtx_("mbs_set_source");
   if (!p || !source) return fail(MBS_EINVAL, "null argument");
   const int64_t nv = nvox(p);
   const cudaMemcpyKind kind = is_device_ptr(source) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -1347,6 +1662,27 @@ mbs_status mbs_set_source(mbs_plan* p, const void* source) {
   if (p->graph_ready) {  // the captured graph holds the source box: capture again
     cudaGraphExecDestroy(p->graph);
     p->graph_ready = false;
+  }
+  if (p->act_dev) {
+    // activation: only the subdomains meeting the source's bounding box start;
+    // e of the others must read as zero in the neighbours' corrections
+    const int nsub = p->S[0] * p->S[1] * p->S[2];
+    p->act_host.assign(nsub, 0);
+    int any = 0;
+    for (int sidx = 0; sidx < nsub && box[1] >= 0; sidx++) {
+      const int j[3] = {sidx / (p->S[1] * p->S[2]), (sidx / p->S[2]) % p->S[1], sidx % p->S[2]};
+      bool in = true;
+      for (int d = 0; d < 3; d++) {
+        const int lo = p->offs[d][j[d]], hi = lo + p->sizes[d][j[d]];
+        in = in && box[2 * d] < hi && box[2 * d + 1] > lo;
+      }
+      p->act_host[sidx] = in ? 1 : 0;
+      any += in ? 1 : 0;
+    }
+    CU(cudaMemcpyAsync(p->act_dev, p->act_host.data(), nsub * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+    if (p->ebuf) CU(launch_zero(p->ebuf, nv, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    p->act_on = any < nsub;
   }
   if (p->resform) {  // r'_0 = Gamma^-1 (A 0 - y) = -Gamma^-1 y, x_0 = 0 (hi and lo words)
     CU(cudaMemsetAsync(p->xlo, 0, nv * sizeof(unsigned), p->stream));
@@ -1392,6 +1728,8 @@ mbs_status mbs_set_initial_field(mbs_plan* p, const void* x0) {
     if (st) return st;
     CU(launch_negate_copy(p->r, p->r, nv, p->stream));
   }
+  st = activate_all(p);  // a warm start may have field everywhere
+  if (st) return st;
   CU(launch_state_arm(p->state, 0, 0.0, 1, kHistCap, p->stream));
   CU(cudaMemcpyAsync(p->host_state, p->state, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream));
   CU(cudaStreamSynchronize(p->stream));
@@ -1405,6 +1743,7 @@ mbs_status mbs_set_initial_field(mbs_plan* p, const void* x0) {
 mbs_status mbs_iterate(mbs_plan* p, int32_t n_iter, double tol, int32_t no_poll, int32_t* iters_done,
                        double* residual) {
   g_err.clear();
+  NvtxRange nvtx_("mbs_iterate");
   if (!p) return fail(MBS_EINVAL, "null plan");
   if (n_iter < 0) return fail(MBS_EINVAL, "n_iter must be >= 0");
   CU(launch_state_arm(p->state, n_iter, tol, 0, kHistCap, p->stream));
@@ -1412,19 +1751,31 @@ mbs_status mbs_iterate(mbs_plan* p, int32_t n_iter, double tol, int32_t no_poll,
   const bool use_graph = !(p->flags & MBS_FLAG_NO_GRAPH) && !plain;
   int remaining = plain ? 0 : n_iter;
   DevState hs;
+  int target = -1;  // iteration count at which the budget ends (subdomain activation restarts)
+  if (p->act_on) {
+    mbs_status st = read_state(p, &hs);
+    if (st) return st;
+    target = hs.iter + n_iter;
+  }
+restart:
   if (plain) {
     mbs_status st = iterate_plain(p, n_iter, tol, &hs);
     if (st) return st;
   }
+  // subdomain activation needs the host between replays until every subdomain is active
   if (use_graph && remaining >= p->graph_iters) {
-    mbs_status st = ensure_graph(p);
-    if (st) return st;
     while (remaining >= p->graph_iters) {
+      mbs_status st = ensure_graph(p);  // captured again when the activation masks are dropped
+      if (st) return st;
       CU(cudaGraphLaunch(p->graph, p->stream));
       remaining -= p->graph_iters;
-      if (!no_poll) {
+      if (!no_poll || p->act_on) {
         st = read_state(p, &hs);
         if (st) return st;
+        if (p->act_on && !hs.status) {  // also when this call's budget just ran out
+          st = activation_check(p, hs);
+          if (st) return st;
+        }
         if (hs.done) {
           remaining = 0;
           break;
@@ -1435,14 +1786,28 @@ mbs_status mbs_iterate(mbs_plan* p, int32_t n_iter, double tol, int32_t no_poll,
   for (int i = 0; i < remaining; i++) {
     cudaError_t e = enqueue_iteration(p, nullptr);
     if (e) return fail(MBS_ECUDA, std::string("iteration launch: ") + cudaGetErrorString(e));
-    if (!no_poll && (i % 64) == 63) {
+    const bool act = p->act_on && (i + 1) % p->graph_iters == 0;
+    if ((!no_poll && (i % 64) == 63) || act) {
       mbs_status st = read_state(p, &hs);
       if (st) return st;
+      if (act && !hs.status) {
+        st = activation_check(p, hs);
+        if (st) return st;
+      }
       if (hs.done) break;
     }
   }
   mbs_status st = read_state(p, &hs);
   if (st) return st;
+  if (p->act_on && hs.status == 0 && hs.done && hs.iter < target) {
+    // the stop test fired while some subdomains were still inactive: their field
+    // is not part of the solution yet, so activate them all and go on
+    st = activation_check(p, hs, true);
+    if (st) return st;
+    CU(launch_state_arm(p->state, target - hs.iter, tol, 0, kHistCap, p->stream));
+    remaining = target - hs.iter;
+    goto restart;
+  }
   if (iters_done) *iters_done = hs.iter;
   if (residual) *residual = hs.eps;
   if (hs.status == MBS_ENAN) return fail(MBS_ENAN, "residual is not finite");
@@ -1450,6 +1815,20 @@ mbs_status mbs_iterate(mbs_plan* p, int32_t n_iter, double tol, int32_t no_poll,
   if (hs.status == MBS_ETIMEOUT) return fail(MBS_ETIMEOUT, "a bounded wait for a tensor-map copy expired");
   if (hs.iter > 0 && hs.eps < tol) return MBS_OK;
   return MBS_ENOCONV;
+}
+
+mbs_status mbs_get_active_subdomains(const mbs_plan* p, int32_t* flags, int32_t cap, int32_t* n_active) {
+  g_err.clear();
+  if (!p) return fail(MBS_EINVAL, "null plan");
+  const int nsub = p->S[0] * p->S[1] * p->S[2];
+  int na = 0;
+  for (int sidx = 0; sidx < nsub; sidx++) {
+    const int on = (!p->act_dev || sidx >= (int)p->act_host.size()) ? 1 : p->act_host[sidx];
+    if (flags && sidx < cap) flags[sidx] = on;
+    na += on;
+  }
+  if (n_active) *n_active = na;
+  return MBS_OK;
 }
 
 mbs_status mbs_get_field(const mbs_plan* p, void* out) {
@@ -1541,6 +1920,20 @@ mbs_status mbs_profile_iterations(mbs_plan* p, int32_t n_iter, int32_t launches[
 // stream, so the solves' kernels run concurrently; a plan that has converged
 // leaves its kernels at once (its own stop flag).
 // ---------------------------------------------------------------------------
+// One launch of the fused batch: a pass (or correction, layer update) of every
+// plan that has it, for one edge; its argument array sits at `off` in desc_mem.
+struct BatchLaunch {
+  int kind;        // 0 first pass, 1 last pass, 2 axis-1 pass, 3 axis-0 pass, 4 corrections, 5 layer update
+  int n;           // edge (kinds 0-3), axis (kind 4)
+  bool inv;        // axis-1 pass: inverse
+  int m;           // plans in the launch
+  dim3 grid;
+  size_t smem;
+  size_t off;      // byte offset of the argument array
+  long long maxthr;  // kind 4: largest thread count
+  int max_slots;   // kind 5: largest 2 t S_2
+};
+
 struct mbs_batch {
   std::vector<mbs_plan*> plans;
   std::vector<unsigned> gen;
@@ -1552,9 +1945,226 @@ struct mbs_batch {
   bool ready[2];
   int G;
   DevState* host_states;
+  // fused form: one launch per pass and edge over all plans (batch_build)
+  bool fused;
+  int t;
+  void* desc_mem;
+  size_t desc_cap;
+  std::vector<BatchLaunch> launches;
+  // the launches of one pass (one per edge) run side by side on these streams
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> side_done;
+  cudaEvent_t stage;
 };
 
 namespace {
+
+// The fused form of a batch (one launch per pass and edge over all plans,
+// grid.z or grid.y selecting the plan) applies when every plan iterates in the
+// default x form with FP32 corrections, its axis-2 corrections fused into the
+// first pass and the layer update, every subdomain edge a mixed-radix length of
+// at most 128 and at least 2t on the corrected axes 0 and 1, and one t for all.
+// Otherwise the batch replays a graph of every plan's own launches.
+bool batch_fusable(const mbs_batch* b) {
+  const int t = b->plans[0]->t;
+  for (const mbs_plan* p : b->plans) {
+    if (p->t != t || t == 0 || !p->has_shell || p->resform) return false;
+    if (p->flags & (MBS_FLAG_PLAIN_STEPS | MBS_FLAG_CORR_TF32 | MBS_FLAG_ACTIVATION)) return false;
+    if (!fuse_e2(p) || !fused_layer_update(p) || p->device != b->plans[0]->device) return false;
+    for (int d = 0; d < 3; d++)
+      for (int s = 0; s < p->S[d]; s++) {
+        const int n = p->sizes[d][s];
+        if (n > 128 || !fft_size_compiled(n)) return false;
+        if (d < 2 && p->a[d] > 0 && n < 2 * t) return false;
+      }
+  }
+  return true;
+}
+
+// Argument arrays of every fused launch of one iteration, in iteration order,
+// copied to the device (again after any mbs_set_source: they hold the source box).
+mbs_status batch_build(mbs_batch* b) {
+  b->launches.clear();
+  std::vector<char> host;
+  auto push = [&](const void* src, size_t bytes) {
+    const size_t off = (host.size() + 255) & ~size_t(255);
+    host.resize(off + bytes);
+    memcpy(host.data() + off, src, bytes);
+    return off;
+  };
+  const int t = b->t;
+  // corrections of x (kind 4) on axes 0 and 1, then the passes, then the corrections of e
+  auto corr_launches = [&](bool on_e) {
+    for (int d = 0; d < 2; d++) {
+      std::vector<CorrArgs> v;
+      long long maxthr = 0;
+      for (mbs_plan* p : b->plans) {
+        if (p->a[d] <= 0) continue;
+        CorrArgs c;
+        memset(&c, 0, sizeof(c));
+        c.F = on_e ? p->ebuf : p->x;
+        c.C = p->K;
+        c.c = make_float2((float)p->c_re, (float)p->c_im);
+        c.cW = p->cW;
+        c.tb = p->tb;
+        c.g = p->g;
+        c.state = p->state;
+        c.axis = d;
+        c.block = 128;
+        v.push_back(c);
+        const long long npen = d == 0 ? p->N[1] * p->N[2] : p->N[0] * p->N[2];
+        maxthr = std::max(maxthr, 2 * npen * p->S[d]);
+      }
+      if (v.empty()) continue;
+      BatchLaunch L = {};
+      L.kind = 4;
+      L.n = d;
+      L.m = (int)v.size();
+      L.maxthr = maxthr;
+      L.off = push(v.data(), v.size() * sizeof(CorrArgs));
+      b->launches.push_back(L);
+    }
+  };
+  corr_launches(false);
+  // pass kind k over the size groups of axis ax, for every edge n present in any plan
+  auto pass_launches = [&](int kind, int ax, bool inv) {
+    std::map<int, std::vector<PassArgs>> by_n;
+    std::map<int, std::pair<unsigned, unsigned>> ext;  // largest grid x, y per edge
+    for (mbs_plan* p : b->plans) {
+      int poff = 0;
+      const int nrb = nrow_blocks(p);
+      for (size_t gi = 0; gi < p->groups[ax].size(); gi++) {
+        const SizeGroup& gz = p->groups[ax][gi];
+        if ((kind == 2) && gz.n == 1) continue;
+        PassArgs a = base_args(p);
+        a.X = p->x;
+        a.Xout = p->x;
+        a.state = p->state;
+        if (p->have_source) {
+          a.S = p->src;
+          for (int i = 0; i < 6; i++) a.sbox[i] = p->sbox[i];
+        }
+        a.nsub = gz.nsub;
+        memcpy(a.subs, gz.subs, sizeof(a.subs));
+        set_len_tables(p, a, gz.n);
+        unsigned gx = 0, gy = 0;
+        if (kind == 0 || kind == 1) {
+          a.mode = kind == 0 ? FIRST_ITER : LAST_ITER;
+          if (kind == 1) {
+            a.partials = p->partials;
+            a.slot0 = poff;
+            a.n_total = p->n_rows_partials + kShellBlocks;
+            a.fin = nullptr;  // the layer update ends the iteration
+            a.hist = p->history;
+            poff += nrb * gz.nsub;
+          }
+          gx = (unsigned)nrb;
+          gy = (unsigned)gz.nsub;
+        } else {
+          a.mode = MID_PROP;
+          gx = (unsigned)((p->N[2] + 31) / 32);
+          gy = (unsigned)((kind == 2 ? p->N[0] : p->N[1]) * gz.nsub);
+        }
+        by_n[gz.n].push_back(a);
+        auto& e = ext[gz.n];
+        e.first = std::max(e.first, gx);
+        e.second = std::max(e.second, gy);
+      }
+    }
+    for (auto& kv : by_n) {
+      const int n = kv.first;
+      BatchLaunch L = {};
+      L.kind = kind;
+      L.n = n;
+      L.inv = inv;
+      L.m = (int)kv.second.size();
+      L.grid = dim3(ext[n].first, ext[n].second, (unsigned)L.m);
+      L.smem = (size_t)n * 33 * sizeof(float2) + (kind == 0 ? ((size_t)4 * t * 33 + t) * sizeof(float2) : 0);
+      L.off = push(kv.second.data(), kv.second.size() * sizeof(PassArgs));
+      b->launches.push_back(L);
+    }
+  };
+  pass_launches(0, 2, false);
+  pass_launches(2, 1, false);
+  pass_launches(3, 0, false);
+  pass_launches(2, 1, true);
+  pass_launches(1, 2, false);
+  corr_launches(true);
+  {  // the layer update (kind 5) ends every plan's iteration
+    std::vector<ShellArgs> v;
+    int max_slots = 0;
+    for (mbs_plan* p : b->plans) {
+      ShellArgs sa = shell_args(p);
+      sa.state = p->state;
+      sa.mode = SHELL_UPDATE_ITER;
+      sa.partials = p->partials;
+      sa.slot0 = p->n_rows_partials;
+      sa.n_total = p->n_rows_partials + kShellBlocks;
+      sa.fin = p->state;
+      sa.hist = p->history;
+      v.push_back(sa);
+      max_slots = std::max(max_slots, p->a[2] > 0 ? 2 * t * p->S[2] : 0);
+    }
+    BatchLaunch L = {};
+    L.kind = 5;
+    L.m = (int)v.size();
+    L.max_slots = max_slots;
+    L.off = push(v.data(), v.size() * sizeof(ShellArgs));
+    b->launches.push_back(L);
+  }
+  if (host.size() > b->desc_cap) {  // (re)allocate the argument arrays
+    if (b->desc_mem) cudaFree(b->desc_mem);
+    b->desc_mem = nullptr;
+    b->desc_cap = 0;
+    CU(cudaMalloc(&b->desc_mem, host.size()));
+    b->desc_cap = host.size();
+  }
+  CU(cudaMemcpyAsync(b->desc_mem, host.data(), host.size(), cudaMemcpyHostToDevice, b->stream));
+  CU(cudaStreamSynchronize(b->stream));
+  return MBS_OK;
+}
+
+cudaError_t batch_launch_one(mbs_batch* b, const BatchLaunch& L, cudaStream_t st) {
+  const char* base = (const char*)b->desc_mem;
+  if (L.kind <= 3)
+    return launch_pass_batch(L.n, L.kind, L.inv, b->t == 8 ? 8 : 0, (const PassArgs*)(base + L.off), L.grid, L.smem,
+                             st);
+  if (L.kind == 4) return launch_corr_side_batch((const CorrArgs*)(base + L.off), L.m, b->t, L.maxthr, st);
+  return launch_shell_rows_batch((const ShellArgs*)(base + L.off), L.m, b->t, L.max_slots, kShellBlocks, st);
+}
+
+// One iteration of every plan in the fused form. Consecutive launches of the
+// same pass (one per edge: disjoint subdomains, so independent) run side by side
+// on the batch's side streams; the passes follow one another. The correction
+// launches stay in order (axis 1 adds to what axis 0 wrote).
+cudaError_t batch_enqueue_fused(mbs_batch* b) {
+  const size_t nl = b->launches.size();
+  size_t i = 0;
+  while (i < nl) {
+    const BatchLaunch& L0 = b->launches[i];
+    size_t j = i + 1;
+    if (L0.kind <= 3)
+      while (j < nl && b->launches[j].kind == L0.kind && b->launches[j].inv == L0.inv) j++;
+    cudaError_t e;
+    if (j - i == 1 || b->side.empty()) {
+      for (size_t k = i; k < j; k++)
+        if ((e = batch_launch_one(b, b->launches[k], b->stream))) return e;
+    } else {
+      if ((e = cudaEventRecord(b->stage, b->stream))) return e;
+      const size_t ns = std::min(j - i, b->side.size());
+      for (size_t k = 0; k < ns; k++)
+        if ((e = cudaStreamWaitEvent(b->side[k], b->stage, 0))) return e;
+      for (size_t k = i; k < j; k++)
+        if ((e = batch_launch_one(b, b->launches[k], b->side[(k - i) % ns]))) return e;
+      for (size_t k = 0; k < ns; k++) {
+        if ((e = cudaEventRecord(b->side_done[k], b->side[k]))) return e;
+        if ((e = cudaStreamWaitEvent(b->stream, b->side_done[k], 0))) return e;
+      }
+    }
+    i = j;
+  }
+  return cudaSuccess;
+}
 
 mbs_status batch_capture(mbs_batch* b, int which, int iters) {
   if (b->ready[which]) {
@@ -1564,7 +2174,10 @@ mbs_status batch_capture(mbs_batch* b, int which, int iters) {
   cudaGraph_t g;
   CU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaEventRecord(b->fork, b->stream);
-  for (size_t i = 0; i < b->plans.size() && !e; i++) {
+  if (b->fused) {
+    for (int k = 0; k < iters && !e; k++) e = batch_enqueue_fused(b);
+  }
+  for (size_t i = 0; i < b->plans.size() && !e && !b->fused; i++) {
     mbs_plan* p = b->plans[i];
     e = cudaStreamWaitEvent(p->stream, b->fork, 0);
     for (int k = 0; k < iters && !e; k++) e = enqueue_iteration(p, nullptr);
@@ -1599,7 +2212,8 @@ mbs_status mbs_batch_create(mbs_batch** out, int32_t nplans, mbs_plan* const* pl
   *out = nullptr;
   for (int i = 0; i < nplans; i++) {
     if (!plans[i]) return fail(MBS_EINVAL, "null plan in batch");
-    if (plans[i]->flags & MBS_FLAG_PLAIN_STEPS) return fail(MBS_EINVAL, "plain-step plans cannot be batched");
+    if (plans[i]->flags & (MBS_FLAG_PLAIN_STEPS | MBS_FLAG_ACTIVATION))
+      return fail(MBS_EINVAL, "plain-step plans and plans with subdomain activation cannot be batched");
   }
   mbs_batch* b = new mbs_batch();
   b->plans.assign(plans, plans + nplans);
@@ -1609,6 +2223,11 @@ mbs_status mbs_batch_create(mbs_batch** out, int32_t nplans, mbs_plan* const* pl
   b->own_stream = stream == nullptr;
   b->host_states = nullptr;
   b->fork = nullptr;
+  b->desc_mem = nullptr;
+  b->desc_cap = 0;
+  b->t = plans[0]->t;
+  b->fused = batch_fusable(b);
+  b->stage = nullptr;
   if (stream) {
     b->stream = (cudaStream_t)stream;
   } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1618,6 +2237,17 @@ mbs_status mbs_batch_create(mbs_batch** out, int32_t nplans, mbs_plan* const* pl
   b->join.assign(nplans, nullptr);
   bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
             cudaMallocHost((void**)&b->host_states, nplans * sizeof(DevState)) == cudaSuccess;
+  if (ok && b->fused) {  // side streams for the per-edge launches of one pass
+    ok = cudaEventCreateWithFlags(&b->stage, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < 16 && ok; k++) {
+      cudaStream_t sk;
+      cudaEvent_t ek;
+      ok = cudaStreamCreateWithFlags(&sk, cudaStreamNonBlocking) == cudaSuccess;
+      if (ok) b->side.push_back(sk);
+      ok = ok && cudaEventCreateWithFlags(&ek, cudaEventDisableTiming) == cudaSuccess;
+      if (ok) b->side_done.push_back(ek);
+    }
+  }
   for (int i = 0; i < nplans && ok; i++) ok = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     mbs_batch_destroy(b);
@@ -1630,6 +2260,7 @@ mbs_status mbs_batch_create(mbs_batch** out, int32_t nplans, mbs_plan* const* pl
 mbs_status mbs_batch_iterate(mbs_batch* b, int32_t n_iter, double tol, int32_t no_poll, int32_t* iters,
                              double* residuals, int32_t* statuses) {
   g_err.clear();
+  NvtxRange nvtx_("mbs_batch_iterate");
   if (!b || n_iter < 0) return fail(MBS_EINVAL, "bad argument");
   // graphs hold every plan's source box: capture again after any mbs_set_source
   bool stale = false;
@@ -1642,6 +2273,10 @@ mbs_status mbs_batch_iterate(mbs_batch* b, int32_t n_iter, double tol, int32_t n
         b->ready[w] = false;
       }
     for (size_t i = 0; i < b->plans.size(); i++) b->gen[i] = b->plans[i]->source_gen;
+    if (b->fused) {
+      mbs_status st = batch_build(b);  // the argument arrays hold each plan's source box
+      if (st) return st;
+    }
   }
   for (mbs_plan* p : b->plans) CU(launch_state_arm(p->state, n_iter, tol, 0, kHistCap, b->stream));
   int remaining = n_iter;
@@ -1684,6 +2319,26 @@ mbs_status mbs_batch_iterate(mbs_batch* b, int32_t n_iter, double tol, int32_t n
   return worst;
 }
 
+int32_t mbs_batch_launches_per_iteration(mbs_batch* b, int32_t* fused) {
+  g_err.clear();
+  if (!b) return -1;
+  if (fused) *fused = b->fused ? 1 : 0;
+  if (b->fused) {
+    if (b->launches.empty() && batch_build(b)) return -1;
+    return (int32_t)b->launches.size();
+  }
+  int n = 0;  // every plan's own launches: count one captured iteration of each
+  for (mbs_plan* p : b->plans) {
+    int k = 0;
+    if (p->has_shell) k += (p->a[0] > 0) + (p->a[1] > 0) + (fuse_e2(p) ? 0 : (p->a[2] > 0));
+    k += (int)p->groups[2].size() * 2 + (int)p->groups[0].size();
+    for (auto& gy : p->groups[1]) k += gy.n == 1 ? 0 : 2;
+    if (p->has_shell) k += (p->a[0] > 0) + (p->a[1] > 0) + (fused_layer_update(p) ? 0 : (p->a[2] > 0)) + 1;
+    n += k;
+  }
+  return n;
+}
+
 void mbs_batch_destroy(mbs_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
@@ -1693,6 +2348,10 @@ void mbs_batch_destroy(mbs_batch* b) {
   for (cudaEvent_t e : b->join)
     if (e) cudaEventDestroy(e);
   if (b->host_states) cudaFreeHost(b->host_states);
+  if (b->desc_mem) cudaFree(b->desc_mem);
+  for (cudaStream_t sk : b->side) cudaStreamDestroy(sk);
+  for (cudaEvent_t ek : b->side_done) cudaEventDestroy(ek);
+  if (b->stage) cudaEventDestroy(b->stage);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }

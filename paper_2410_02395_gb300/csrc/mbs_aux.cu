@@ -119,13 +119,12 @@ __global__ void __launch_bounds__(128) k_corr_strided(const __grid_constant__ Co
 //   side 0 (first t):  out[q]        = sum_b w[q - b + t - 1] (f_left[n_l-t+b] - f_s[n-t+b])
 //   side 1 (last t):   out[n-t+aa]   = sum_b w[b - aa + t - 1] (f_right[b]      - f_s[b])
 template <int T>
-__global__ void __launch_bounds__(128) k_corr_side(const __grid_constant__ CorrArgs a) {
+__device__ __forceinline__ void corr_side_body(const CorrArgs& a, long long gid) {
   if (a.state && a.state->done) return;
   const int d = a.axis;
   const AxisDesc& ax = a.g.ax[d];
   const long long N0 = a.g.N0, N1 = a.g.N1, N2 = a.g.N2;
   const long long npen = d == 0 ? N1 * N2 : N0 * N2;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= 2 * npen * ax.S) return;
   const int ss = (int)(gid / npen);  // subdomain * 2 + side
   const int s = ss >> 1, side = ss & 1;
@@ -168,6 +167,19 @@ __global__ void __launch_bounds__(128) k_corr_side(const __grid_constant__ CorrA
     }
     put(C, out0 + (long long)q * stride, times_i(vx, vy), add);
   }
+}
+
+template <int T>
+__global__ void __launch_bounds__(128) k_corr_side(const __grid_constant__ CorrArgs a) {
+  corr_side_body<T>(a, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Batched form: plan blockIdx.y of d (threads past its pencils leave at once).
+template <int T>
+__global__ void __launch_bounds__(128) k_corr_side_batch(const CorrArgs* __restrict__ d) {
+  __shared__ CorrArgs a;
+  stage_args(&a, &d[blockIdx.y]);
+  corr_side_body<T>(a, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Axis 2: one warp per grid row; the row's 2t layer values of every subdomain
@@ -264,7 +276,11 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], 
 // TC: the truncation width when known at compile time (t == TP == 8), 0 otherwise.
 template <int TP, int TC>
 __global__ void __launch_bounds__(128) k_corr_tc(const __grid_constant__ CorrArgs a) {
-  __shared__ float As[4][64][TP + 4];  // per warp; +4 keeps the fragment reads conflict-free
+  // per warp, transposed: As[k][row] (row 2p: real part of pencil p, 2p + 1: imaginary part).
+  // The pitch 72 (= 8 mod 32 banks) keeps the fragment reads (8 rows x 4 k per
+  // instruction) conflict-free, and every lane's pencil is one float2 per k, so the
+  // gather and the final reads move 256 contiguous bytes per warp.
+  __shared__ __align__(16) float As[4][TP][72];
   __shared__ float Wr[TP][TP + 1];     // real W (not scaled by c), zero padded
   if (a.state && a.state->done) return;
   const int d = a.axis, t = TC > 0 ? TC : a.g.t;
@@ -314,8 +330,7 @@ __global__ void __launch_bounds__(128) k_corr_tc(const __grid_constant__ CorrArg
       const float2 v = nb >= 0 ? a.F[nb0 + (long long)b * stride] : make_float2(0.f, 0.f);
       g = csub(v, o);
     }
-    As[warp][2 * lane][b] = g.x;
-    As[warp][2 * lane + 1][b] = g.y;
+    *reinterpret_cast<float2*>(&As[warp][b][2 * lane]) = g;
   }
   __syncwarp();
   const int gq = lane >> 2, tg = lane & 3;
@@ -347,7 +362,7 @@ __global__ void __launch_bounds__(128) k_corr_tc(const __grid_constant__ CorrArg
 #pragma unroll
       for (int i = 0; i < 4; i++) {
         const int r = mt * 16 + gq + 8 * (i & 1), k = ks * 8 + tg + 4 * (i >> 1);
-        const float v = As[warp][r][k];
+        const float v = As[warp][k][r];
         ah[i] = tf32_hi(v);
         al[i] = tf32_hi(v - __uint_as_float(ah[i]));
       }
@@ -368,7 +383,7 @@ __global__ void __launch_bounds__(128) k_corr_tc(const __grid_constant__ CorrArg
 #pragma unroll
       for (int i = 0; i < 4; i++) {
         const int r = mt * 16 + gq + 8 * (i >> 1), q = nt * 8 + 2 * tg + (i & 1);
-        As[warp][r][q] = D[mt][nt][i];
+        As[warp][q][r] = D[mt][nt][i];
       }
   __syncwarp();
   if (!valid) return;
@@ -381,12 +396,12 @@ __global__ void __launch_bounds__(128) k_corr_tc(const __grid_constant__ CorrArg
     for (int q = 0; q < TC; q++) prev[q] = add ? a.C[out0 + (long long)q * stride] : make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < TC; q++) {
-      const float2 v = cmul(c, make_float2(As[warp][2 * lane][q], As[warp][2 * lane + 1][q]));
+      const float2 v = cmul(c, *reinterpret_cast<const float2*>(&As[warp][q][2 * lane]));
       a.C[out0 + (long long)q * stride] = cadd(prev[q], v);
     }
   } else {
     for (int q = 0; q < t; q++) {
-      const float2 v = cmul(c, make_float2(As[warp][2 * lane][q], As[warp][2 * lane + 1][q]));
+      const float2 v = cmul(c, *reinterpret_cast<const float2*>(&As[warp][q][2 * lane]));
       put(a.C, out0 + (long long)q * stride, v, add);
     }
   }
@@ -478,14 +493,15 @@ cudaError_t launch_corr_t(const CorrArgs& a, cudaStream_t st) {
     return cudaGetLastError();
   }
   const long long npen = a.axis == 0 ? a.g.N1 * a.g.N2 : a.g.N0 * a.g.N2;
-  bool split = true;
+  bool split = a.variant == 0;
   for (int s = 0; s < ax.S; s++) split = split && ax.n[s] >= 2 * T;
+  const int bs = a.block == 64 ? 64 : 128;
   if (split) {
-    const unsigned blocks = (unsigned)((2 * npen * ax.S + 127) / 128);
-    k_corr_side<T><<<blocks, 128, 0, st>>>(a);
+    const unsigned blocks = (unsigned)((2 * npen * ax.S + bs - 1) / bs);
+    k_corr_side<T><<<blocks, bs, 0, st>>>(a);
   } else {
-    const unsigned blocks = (unsigned)((npen * ax.S + 127) / 128);
-    k_corr_strided<T><<<blocks, 128, 0, st>>>(a);
+    const unsigned blocks = (unsigned)((npen * ax.S + bs - 1) / bs);
+    k_corr_strided<T><<<blocks, bs, 0, st>>>(a);
   }
   return cudaGetLastError();
 }
@@ -704,8 +720,9 @@ __device__ __forceinline__ float2 layer_step(float2 b, float2 e, float2 corr, fl
   return make_float2(fmaf(-alpha, r.x, x.x), fmaf(-alpha, r.y, x.y));
 }
 
+// bx, nx: this block and the block count of the plan's launch (the loops stride by nx).
 template <int MODE, int TC, int J>
-__global__ void __launch_bounds__(256, J == 1 ? 4 : 3) k_shell_rows(const __grid_constant__ ShellArgs a) {
+__device__ __forceinline__ void shell_rows_body(const ShellArgs& a, unsigned bx, unsigned nx) {
   extern __shared__ float2 ws[];  // [8 warps][2 rows][M] staged e
   __shared__ double red[8];
   __shared__ float w[2 * kMaxT];  // w[m] = Im(c W) at column - row = m - (t - 1)
@@ -729,7 +746,7 @@ __global__ void __launch_bounds__(256, J == 1 ? 4 : 3) k_shell_rows(const __grid
     const unsigned nl0 = (unsigned)a.tb.nl0, nl1 = (unsigned)a.tb.nl1;
     const unsigned f0 = nl0 * N1;
     const unsigned nfull = f0 + ((unsigned)a.g.N0 - nl0) * nl1;
-    for (unsigned fr = blockIdx.x * 8u + warp; fr < nfull; fr += gridDim.x * 8u) {
+    for (unsigned fr = bx * 8u + warp; fr < nfull; fr += nx * 8u) {
       unsigned i0, i1;
       if (fr < f0) {
         i0 = (unsigned)a.tb.l0[fr / N1];
@@ -744,13 +761,14 @@ __global__ void __launch_bounds__(256, J == 1 ? 4 : 3) k_shell_rows(const __grid
       const float2* Er = a.E + rb;
       const float2* __restrict__ Br = a.B + rb;
       float2* Xr = a.X + rb;
+      const int j0 = a.active ? a.tb.sub[0][i0] : 0, j1 = a.active ? a.tb.sub[1][i1] : 0;
       for (unsigned k0 = lane; k0 < n2; k0 += 32 * U) {
         float2 e[U], c[U], b[U], x[U];
         bool ok[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
           const unsigned k = k0 + 32 * u;
-          ok[u] = k < n2 && !sh2[k];
+          ok[u] = k < n2 && !sh2[k] && (!a.active || sub_active(a.active, a.g, j0, j1, a.tb.sub[2][k]));
           if (ok[u]) {
             c[u] = Cr[k];
             e[u] = Er[k];
@@ -781,14 +799,18 @@ __global__ void __launch_bounds__(256, J == 1 ? 4 : 3) k_shell_rows(const __grid
       if (k >= t && qj[j] < t) use[j] = false;  // n < 2t: the voxel is the first-range slot q (still staged)
     }
     const unsigned rows = (unsigned)(a.g.N0 * a.g.N1);
-    const unsigned step = gridDim.x * 8u;
-    for (unsigned rho0 = blockIdx.x * 8u + warp; rho0 < rows; rho0 += 2 * step) {
+    const unsigned step = nx * 8u;
+    for (unsigned rho0 = bx * 8u + warp; rho0 < rows; rho0 += 2 * step) {
       const unsigned rho1 = rho0 + step;
       const bool live1 = rho1 < rows;
       const unsigned i00 = rho0 / N1, i10 = rho0 - i00 * N1;
       const unsigned i01 = live1 ? rho1 / N1 : 0, i11 = live1 ? rho1 - i01 * N1 : 0;
       const bool full0 = a.tb.shell[0][i00] | a.tb.shell[1][i10];
       const bool full1 = live1 && (a.tb.shell[0][i01] | a.tb.shell[1][i11]);
+      // subdomains along axes 0, 1 of the two rows (activation: inactive slots keep x = 0; their
+      // e, zero, still enters the neighbours' corrections)
+      const int r00 = a.active ? a.tb.sub[0][i00] : 0, r10 = a.active ? a.tb.sub[1][i10] : 0;
+      const int r01 = a.active && live1 ? a.tb.sub[0][i01] : 0, r11 = a.active && live1 ? a.tb.sub[1][i11] : 0;
       const long long rb0 = (long long)rho0 * n2, rb1 = (long long)rho1 * n2;
       float2 e0[J], b0[J], x0[J], c0[J], e1[J], b1[J], x1[J], c1[J];
 #pragma unroll
@@ -821,14 +843,14 @@ __global__ void __launch_bounds__(256, J == 1 ? 4 : 3) k_shell_rows(const __grid
         if (!use[j]) continue;
         const int s = sj[j], lft = ax.left[s], rgt = ax.right[s];
         const long long o = ax.off[s] + qj[j];
-        {
+        if (sub_active(a.active, a.g, r00, r10, s)) {
           const float2* ev = evw;
           const float2 corr = axis2_corr_sum<TC>(w, t, qj[j], ax.n[s], ev + s * 2 * t,
                                                  lft >= 0 ? ev + lft * 2 * t + t : nullptr,
                                                  rgt >= 0 ? ev + rgt * 2 * t : nullptr);
           a.X[rb0 + o] = layer_step<MODE>(b0[j], e0[j], cadd(c0[j], corr), x0[j], a.alpha, racc);
         }
-        if (live1) {
+        if (live1 && sub_active(a.active, a.g, r01, r11, s)) {
           const float2* ev = evw + M;
           const float2 corr = axis2_corr_sum<TC>(w, t, qj[j], ax.n[s], ev + s * 2 * t,
                                                  lft >= 0 ? ev + lft * 2 * t + t : nullptr,
@@ -842,8 +864,20 @@ __global__ void __launch_bounds__(256, J == 1 ? 4 : 3) k_shell_rows(const __grid
   }
   if (a.partials) {
     const double sum = block_sum(acc, red);
-    finish_block(Finish{a.partials, a.slot0, a.n_total, a.fin, a.hist}, sum, red);
+    finish_block_at(Finish{a.partials, a.slot0, a.n_total, a.fin, a.hist}, sum, red, bx, nx);
   }
+}
+
+template <int MODE, int TC, int J>
+__global__ void __launch_bounds__(256, J == 1 ? 4 : 3) k_shell_rows(const __grid_constant__ ShellArgs a) {
+  shell_rows_body<MODE, TC, J>(a, blockIdx.x, gridDim.x);
+}
+
+template <int MODE, int TC, int J>
+__global__ void __launch_bounds__(256, J == 1 ? 4 : 3) k_shell_rows_batch(const ShellArgs* __restrict__ d) {
+  __shared__ ShellArgs a;
+  stage_args(&a, &d[blockIdx.y]);
+  shell_rows_body<MODE, TC, J>(a, blockIdx.x, gridDim.x);
 }
 
 bool shell_rows_supported(const GridDesc& g) {
@@ -872,6 +906,39 @@ cudaError_t launch_shell_rows(const ShellArgs& a, int blocks, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Batched layer update of the iteration (x form, SHELL_UPDATE_ITER) over the
+// plans of d (grid blocks x m); every plan must fit the fused form, with t and
+// the row-pair staging (M <= 32 or not) given for all of them.
+cudaError_t launch_shell_rows_batch(const ShellArgs* d, int m, int t, int max_slots, int blocks, cudaStream_t st) {
+  const size_t smem = (size_t)8 * 2 * max_slots * sizeof(float2);
+  const dim3 grid((unsigned)blocks, (unsigned)m);
+  const bool t8 = t == 8, one = max_slots <= 32;
+  if (t8 && one) k_shell_rows_batch<SHELL_UPDATE_ITER, 8, 1><<<grid, 256, smem, st>>>(d);
+  else if (t8) k_shell_rows_batch<SHELL_UPDATE_ITER, 8, 2><<<grid, 256, smem, st>>>(d);
+  else if (one) k_shell_rows_batch<SHELL_UPDATE_ITER, 0, 1><<<grid, 256, smem, st>>>(d);
+  else k_shell_rows_batch<SHELL_UPDATE_ITER, 0, 2><<<grid, 256, smem, st>>>(d);
+  return cudaGetLastError();
+}
+
+// Batched FP32 edge corrections of one axis (0 or 1) with the side-split kernel
+// (every subdomain edge on the axis >= 2t) over the plans of d; max_threads: the
+// largest 2 * pencils * subdomains of the plans.
+cudaError_t launch_corr_side_batch(const CorrArgs* d, int m, int t, long long max_threads, cudaStream_t st) {
+  const dim3 grid((unsigned)((max_threads + 127) / 128), (unsigned)m);
+  switch (t) {
+#define MBS_TB(T)                                         \
+  case T:                                                 \
+    k_corr_side_batch<T><<<grid, 128, 0, st>>>(d);        \
+    return cudaGetLastError();
+    MBS_TB(1) MBS_TB(2) MBS_TB(3) MBS_TB(4) MBS_TB(5) MBS_TB(6) MBS_TB(7) MBS_TB(8)
+    MBS_TB(9) MBS_TB(10) MBS_TB(11) MBS_TB(12) MBS_TB(13) MBS_TB(14) MBS_TB(15) MBS_TB(16)
+    MBS_TB(20) MBS_TB(24) MBS_TB(32)
+#undef MBS_TB
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_shell(const ShellArgs& a, int blocks, cudaStream_t st) {
   switch (a.mode) {
     case SHELL_UPDATE_ITER: k_shell<SHELL_UPDATE_ITER><<<blocks, 256, 0, st>>>(a); break;
@@ -880,6 +947,71 @@ cudaError_t launch_shell(const ShellArgs& a, int blocks, cudaStream_t st) {
     case SHELL_ADD_E: k_shell<SHELL_ADD_E><<<blocks, 256, 0, st>>>(a); break;
     default: k_shell<SHELL_SET_E><<<blocks, 256, 0, st>>>(a); break;
   }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Activation check (Sec. 3.1, "Implementation"): squared norm of the field an
+// active neighbour transfers into an inactive subdomain's boundary layers.
+// Block row y handles face y; its threads walk the face's pencils along the
+// face axis. The transfer from a left neighbour is c W^T on its last t layers,
+// from a right neighbour c W on its first t layers; with c W = i w (w real) its
+// squared modulus is |w v|^2.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_act_norms(const float2* __restrict__ X, const ActFace* faces, GridDesc g,
+                                                   const float2* __restrict__ cW, double* norms) {
+  __shared__ float w[2 * kMaxT];
+  __shared__ double red[8];
+  const int t = g.t;
+  if (threadIdx.x < 2 * t - 1) {
+    const int m = threadIdx.x, aa = m < t - 1 ? t - 1 - m : 0, bb = aa + m - (t - 1);
+    w[m] = cW[aa * t + bb].y;
+  }
+  __syncthreads();
+  const ActFace f = faces[blockIdx.y];
+  const int d = f.axis;
+  int jn[3];  // the neighbour's subdomain coordinates
+  {
+    const int S1 = g.ax[1].S, S2 = g.ax[2].S;
+    jn[0] = f.nb / (S1 * S2);
+    jn[1] = (f.nb / S2) % S1;
+    jn[2] = f.nb % S2;
+  }
+  const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;  // the two face axes
+  const long long st[3] = {g.N1 * g.N2, g.N2, 1};
+  const int na = g.ax[da].n[jn[da]], nb = g.ax[db].n[jn[db]];
+  const long long org = (long long)g.ax[da].off[jn[da]] * st[da] + (long long)g.ax[db].off[jn[db]] * st[db];
+  const int nd = g.ax[d].n[jn[d]];
+  const long long l0 = (long long)(g.ax[d].off[jn[d]] + (f.left ? nd - t : 0)) * st[d];
+  float acc = 0.f;
+  double dacc = 0.0;
+  for (long long pp = (long long)blockIdx.x * blockDim.x + threadIdx.x; pp < (long long)na * nb;
+       pp += (long long)gridDim.x * blockDim.x) {
+    const long long ia = pp / nb, ib = pp - ia * nb;
+    const long long base = org + ia * st[da] + ib * st[db] + l0;
+    for (int q = 0; q < t; q++) {
+      float vx = 0.f, vy = 0.f;
+      for (int b = 0; b < t; b++) {
+        const float2 xv = X[base + (long long)b * st[d]];
+        // left neighbour: row q of W^T (W[b][q]); right neighbour: row q of W (W[q][b])
+        const float wv = f.left ? w[q - b + t - 1] : w[b - q + t - 1];
+        vx = fmaf(wv, xv.x, vx);
+        vy = fmaf(wv, xv.y, vy);
+      }
+      acc = fmaf(vx, vx, fmaf(vy, vy, acc));
+    }
+    dacc += (double)acc;  // FP32 over one pencil's t outputs, then FP64
+    acc = 0.f;
+  }
+  const double s = block_sum(dacc, red);
+  if (threadIdx.x == 0 && s > 0.0) atomicAdd(norms + f.s, s);
+}
+
+cudaError_t launch_act_norms(const float2* X, const ActFace* faces, int nfaces, const GridDesc& g, const float2* cW,
+                             double* norms, cudaStream_t st) {
+  if (nfaces <= 0) return cudaSuccess;
+  const dim3 grid(64, (unsigned)nfaces);
+  k_act_norms<<<grid, 256, 0, st>>>(X, faces, g, cW, norms);
   return cudaGetLastError();
 }
 

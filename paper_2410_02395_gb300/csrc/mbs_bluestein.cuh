@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(32 * warps_for(M), fft_min_blocks(M)) k_rows_f
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.bl_n;
   const int off2 = a.g.ax[2].off[a.subs[blockIdx.y]];
-  const RowTile rt = setup_rows(masks, a, off2);
+  const RowTile rt = setup_rows(masks, a, off2, a.subs[blockIdx.y], blockIdx.x);
   const bool iter = a.mode == FIRST_ITER;
   for (int idx = tid; idx < 32 * n; idx += NT) {
     const int r = idx / n, e = idx - r * n;
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(32 * warps_for(M), fft_min_blocks(M)) k_rows_l
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.bl_n;
   const int off2 = a.g.ax[2].off[a.subs[blockIdx.y]];
-  const RowTile rt = setup_rows(masks, a, off2);
+  const RowTile rt = setup_rows(masks, a, off2, a.subs[blockIdx.y], blockIdx.x);
   for (int idx = tid; idx < 32 * n; idx += NT) {
     const int r = idx / n, e = idx - r * n;
     sm[e][r] = rt.ok(r) ? a.K[rt.base(r) + e] : make_float2(0.f, 0.f);
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(32 * warps_for(M), fft_min_blocks(M)) k_mid_bl
   if (a.state && a.state->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n = a.bl_n;
-  const MidPencil m = mid_pencil(a);
+  const MidPencil m = mid_pencil(a, blk_here());
   const int mode = a.mode;
   const float scl = mode == MID_INV ? m.sc : 1.f;
   for (int e = warp; e < n; e += W)

@@ -5,6 +5,7 @@
 namespace mbs {
 #define MBS_DECLARE_GROUP(k)                                                                           \
   bool fft_group_##k(int, int, int, bool, const PassArgs&, int, cudaStream_t, cudaError_t*);           \
+  bool fft_group_##k##_batch(int, int, bool, int, const PassArgs*, dim3, size_t, cudaStream_t, cudaError_t*); \
   bool fft_group_##k##_has(int);
 MBS_FFT_GROUP_IDS(MBS_DECLARE_GROUP)
 #undef MBS_DECLARE_GROUP
@@ -55,4 +56,14 @@ cudaError_t launch_strided(int n, int axis, bool inv, const PassArgs& a, cudaStr
   return dispatch(n, 2, axis, inv, a, 0, st);
 }
 cudaError_t launch_mid(int n, const PassArgs& a, cudaStream_t st) { return dispatch(n, 3, 0, false, a, 0, st); }
+
+cudaError_t launch_pass_batch(int n, int kind, bool inv, int tc, const PassArgs* d, dim3 grid, size_t smem,
+                              cudaStream_t st) {
+  cudaError_t err = cudaErrorInvalidValue;
+#define MBS_TRY_BATCH(k) \
+  if (fft_group_##k##_batch(n, kind, inv, tc, d, grid, smem, st, &err)) return err;
+  MBS_FFT_GROUP_IDS(MBS_TRY_BATCH)
+#undef MBS_TRY_BATCH
+  return cudaErrorInvalidValue;
+}
 }  // namespace mbs

@@ -2,6 +2,8 @@
 // MBS_FFT_GROUP = k and gets
 //   bool fft_group_<k>(n, kind, axis, inv, args, row blocks, stream, &err)
 //     launches the pass kernel of that kind for edge n when n is in group k;
+//   bool fft_group_<k>_batch(n, kind, inv, tc, descriptors, grid, smem, stream, &err)
+//     the batched form of a pass for edge n (see run_size_batch);
 //   bool fft_group_<k>_has(n)
 //     whether n is in group k.
 #pragma once
@@ -21,6 +23,14 @@ bool MBS_CAT(fft_group_, MBS_FFT_GROUP)(int n, int kind, int axis, bool inv, con
                                         cudaStream_t st, cudaError_t* err) {
   switch (n) {
     MBS_CAT(MBS_FFT_GROUP_, MBS_FFT_GROUP)(MBS_CASE)
+    default:
+      return false;
+  }
+}
+bool MBS_CAT(MBS_CAT(fft_group_, MBS_FFT_GROUP), _batch)(int n, int kind, bool inv, int tc, const PassArgs* d, dim3 grid,
+                                                          size_t smem, cudaStream_t st, cudaError_t* err) {
+  switch (n) {
+    MBS_CAT(MBS_FFT_GROUP_, MBS_FFT_GROUP)(MBS_CASE_BATCH)
     default:
       return false;
   }

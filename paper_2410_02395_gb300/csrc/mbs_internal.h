@@ -100,6 +100,8 @@ struct PassArgs {
   int nsub;             // subdomains (along the pass axis) of this size
   int subs[kMaxSplit];
   long long tma_wait;   // bound of a TMA tile wait in SM clock cycles (0: about 2 s)
+  const int* active;    // subdomain activation (Sec. 3.1): null (all active) or one flag per subdomain
+  int tma_ctas;         // resident CTAs per SM of a persistent TMA-fed pass (0: as many as fit)
 };
 
 // Edge corrections E_d F of one axis, written (or, where an earlier axis has
@@ -115,6 +117,11 @@ struct CorrArgs {
   GridDesc g;
   const DevState* state;
   int axis;
+  // launch shape of the FP32 axis-0/1 kernels (chosen by the plan's tuner; the
+  // arithmetic is the same): 0 one thread per (pencil, subdomain, side) where
+  // every edge on the axis is >= 2t, 1 one thread per (pencil, subdomain)
+  int variant;
+  int block;            // threads per block: 64 or 128 (0: 128)
 };
 
 // Voxels of the boundary layers: E = C[v], then the mode's update.
@@ -135,6 +142,7 @@ struct ShellArgs {
   const DevState* state;
   int mode;
   const float2* cW;     // c W (t x t), for the fused axis-2 corrections of launch_shell_rows
+  const int* active;    // subdomain activation: null (all active) or one flag per subdomain
 };
 
 // One step of the plain form of the iteration (MBS_FLAG_PLAIN_STEPS): every
@@ -164,6 +172,42 @@ struct PlainArgs {
 constexpr int kPlainBlocks = 152 * 8;
 cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t st);
 
+#ifdef __CUDACC__
+// Subdomain activation (Sec. 3.1, "Implementation"): with flags, subdomain
+// (j0, j1, j2) is computed only while act[(j0 S1 + j1) S2 + j2] is set; the
+// field of an inactive subdomain stays zero.
+__device__ __forceinline__ bool sub_active(const int* act, const GridDesc& g, int j0, int j1, int j2) {
+  return !act || act[(j0 * g.ax[1].S + j1) * g.ax[2].S + j2] != 0;
+}
+
+// A batched launch reads each plan's arguments from a device array. The CTA
+// copies its plan's arguments to shared memory first: read through a global
+// reference, every field would be loaded again after each store to global
+// memory (the compiler cannot rule out that the store changed it). Every thread
+// of the CTA must call it; it ends with a barrier.
+template <class T>
+__device__ __forceinline__ void stage_args(T* dst, const T* src) {
+  static_assert(sizeof(T) % sizeof(unsigned) == 0, "argument blocks are whole words");
+  const unsigned* s = reinterpret_cast<const unsigned*>(src);
+  unsigned* d = reinterpret_cast<unsigned*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(T) / sizeof(unsigned)); i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+}
+#endif
+
+// Activation check: for every inactive subdomain next to an active one, the
+// squared norm of the field the active neighbours transfer into its boundary
+// layers (Sec. 3.1 steps 1-2 and 5: P = c W x[first t] from the right neighbour,
+// Q = c W^T x[last t] from the left one), added into norms[s].
+struct ActFace {
+  int s;       // the inactive subdomain (linear index)
+  int nb;      // its active neighbour (linear index)
+  int axis;    // axis of the shared face
+  int left;    // 1: the neighbour is on the left (its last t layers transfer), 0: on the right
+};
+cudaError_t launch_act_norms(const float2* X, const ActFace* faces, int nfaces, const GridDesc& g, const float2* cW,
+                             double* norms, cudaStream_t st);
+
 // Launchers (return cudaGetLastError of the launch).
 cudaError_t launch_rows_first(int n, const PassArgs& a, int nrows_blocks, cudaStream_t st);
 cudaError_t launch_rows_last(int n, const PassArgs& a, int nrows_blocks, cudaStream_t st);
@@ -175,6 +219,8 @@ cudaError_t launch_mid(int n, const PassArgs& a, cudaStream_t st);
 bool tma_len_supported(int n);
 bool make_tma_map(CUtensorMap* tm, void* K, const GridDesc& g, int axis, int n);
 cudaError_t launch_strided_tma(int n, int axis, bool inv, const PassArgs& a, const CUtensorMap& tm, cudaStream_t st);
+// Resident CTAs per SM the TMA-fed pass of edge n can have (kind 2: axis 1, 3: axis 0).
+int tma_max_ctas(int n, int kind);
 // TMA-fed axis-0 pass (forward transform, propagator or symbol of L, inverse):
 // modes MID_PROP and MID_LSYM, tensor map made with axis 0.
 cudaError_t launch_mid_tma(int n, const PassArgs& a, const CUtensorMap& tm, cudaStream_t st);
@@ -196,6 +242,14 @@ cudaError_t launch_shell(const ShellArgs& a, int blocks, cudaStream_t st);
 bool shell_rows_supported(const GridDesc& g);
 cudaError_t launch_shell_rows(const ShellArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_state_arm(DevState* state, int add_iter, double tol, int reset, int hist_cap, cudaStream_t st);
+
+// Batched launches: several plans' kernels of one pass in one grid, each plan's
+// arguments in a device array (see mbs_batch_* in mbs_api.cu). kind: 0 first
+// pass, 1 last pass, 2 axis-1 pass, 3 axis-0 pass; edges up to 128.
+cudaError_t launch_pass_batch(int n, int kind, bool inv, int tc, const PassArgs* d, dim3 grid, size_t smem,
+                              cudaStream_t st);
+cudaError_t launch_corr_side_batch(const CorrArgs* d, int m, int t, long long max_threads, cudaStream_t st);
+cudaError_t launch_shell_rows_batch(const ShellArgs* d, int m, int t, int max_slots, int blocks, cudaStream_t st);
 
 // Plan set-up kernels (FP64 arithmetic on the device).
 cudaError_t launch_k2_bounds(const float2* n, GridDesc g, const int* widths, double kappa, double lambda,

@@ -92,16 +92,25 @@ struct RowTile {
   __device__ __forceinline__ bool in_src(int r) const { return (src >> r) & 1u; }
 };
 
-__device__ __forceinline__ RowTile setup_rows(unsigned* masks, const PassArgs& a, int off2) {
+// A CTA's coordinates in the grid of one plan's launch: the block itself in a
+// single-plan launch, or the plan-local block of a batched launch (several
+// plans' passes of the same edge in one grid, grid.z selecting the plan).
+struct Blk {
+  unsigned x, y, z, nx, ny;
+};
+__device__ __forceinline__ Blk blk_here() { return Blk{blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y}; }
+
+// Rows of inactive subdomains (subdomain activation) count as outside the grid.
+__device__ __forceinline__ RowTile setup_rows(unsigned* masks, const PassArgs& a, int off2, int j2, unsigned bx) {
   const int tid = threadIdx.x;
-  const long long rho0 = (long long)blockIdx.x * 32;
+  const long long rho0 = (long long)bx * 32;
   if (tid < 32) {
     const long long rows = a.g.N0 * a.g.N1;
     const long long rho = rho0 + tid;
     bool v = false, l = false, sr = false;
     if (rho < rows) {
       const long long i0 = rho / a.g.N1, i1 = rho - i0 * a.g.N1;
-      v = true;
+      v = sub_active(a.active, a.g, a.tb.sub[0][i0], a.tb.sub[1][i1], j2);
       l = a.tb.shell[0][i0] | a.tb.shell[1][i1];
       sr = a.S && i0 >= a.sbox[0] && i0 < a.sbox[1] && i1 >= a.sbox[2] && i1 < a.sbox[3];
     }
@@ -133,6 +142,13 @@ __device__ __forceinline__ bool in_layer2(const PassArgs& a, int e) {
 // When NT divides 32 N and N divides NT (NT = 2N for every N >= 64 that is a
 // multiple of 16), each thread keeps one element index e and walks rows
 // r, r + NT/N, ...; the rows stay below 32 for k < 32 N / NT.
+// Staged voxels per thread and chunk in the row passes: CH loads of each
+// array in flight per thread. Edges above 256 run two CTAs per SM with at most
+// 48 registers, where the first pass (x, B and E x staged) spills less with a
+// chunk of 4: on the 1280^3 workload it went from 11.4 to 10.7 ms, while the
+// last pass (only the FFT buffer staged) went from 12.5 to 14.3 ms and keeps 8.
+__host__ __device__ constexpr int row_chunk(int pert, int ch) { return pert < ch ? pert : ch; }
+
 template <int N, int NT>
 struct TileMap {
   static constexpr bool fixed = (NT % N) == 0 && ((32 * N) % NT) == 0;
@@ -156,19 +172,20 @@ struct TileMap {
 // ---------------------------------------------------------------------------
 // TC: compile-time truncation width of the fused axis-2 corrections (0: runtime t).
 template <int N, int TC>
-__global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_first(const __grid_constant__ PassArgs a) {
+__device__ __forceinline__ void rows_first_body(const PassArgs& a, const Blk& bk) {
   constexpr int W = warps_for(N);
   constexpr int NT = 32 * W;
   constexpr int PERT = (32 * N + NT - 1) / NT;
-  constexpr int CH = PERT < 8 ? PERT : 8;
+  constexpr int CH = row_chunk(PERT, N > 256 ? 4 : 8);
   extern __shared__ float2 dyn[];
   float2 (*sm)[kPad] = tile_of<N>(dyn);
   __shared__ unsigned masks[3];
   if (a.state && a.state->done) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int j2 = a.subs[blockIdx.y];
+  const int j2 = a.subs[bk.y];
   const int off2 = a.g.ax[2].off[j2];
-  const RowTile rt = setup_rows(masks, a, off2);
+  const RowTile rt = setup_rows(masks, a, off2, j2, bk.x);
+  if (rt.valid == 0u) return;  // every row of the tile inside inactive subdomains
   const bool iter = a.mode == FIRST_ITER;
   // The tile's 32 rows x N elements lie within 32 * N2 <= 2^18 voxels of its
   // origin, so in-tile offsets are 32-bit.
@@ -319,145 +336,188 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_f
   }
 }
 
+// Row tiles of one plan's pass: (N0 N1 + 31) / 32 along x, the subdomain slots along y.
+__device__ __forceinline__ unsigned row_blocks(const PassArgs& a) { return (unsigned)((a.g.N0 * a.g.N1 + 31) / 32); }
+
+template <int N, int TC>
+__global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_first(const __grid_constant__ PassArgs a) {
+  rows_first_body<N, TC>(a, blk_here());
+}
+
+// Batched form: plan blockIdx.z of `d`; blocks past that plan's extent leave at once.
+template <int N, int TC>
+__global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_first_batch(const PassArgs* __restrict__ d) {
+  __shared__ PassArgs a;
+  const PassArgs& ga = d[blockIdx.z];
+  const unsigned nx = row_blocks(ga), ny = (unsigned)ga.nsub;
+  if (blockIdx.x >= nx || blockIdx.y >= ny) return;
+  stage_args(&a, &ga);
+  rows_first_body<N, TC>(a, Blk{blockIdx.x, blockIdx.y, 0u, nx, ny});
+}
+
 // ---------------------------------------------------------------------------
 // Axis-2 inverse pass with the fused update epilogue (Eq. wavesim_iter):
 // e = x - w; away from the boundary layers r = B e, x <- x - alpha r and the
 // FP64 |r|^2; on the layers e is stored for the correction step.
 // ---------------------------------------------------------------------------
 template <int N, bool RES>
-__global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_last(const __grid_constant__ PassArgs a) {
+__device__ __forceinline__ void rows_last_body(const PassArgs& a, const Blk& bk) {
   constexpr int W = warps_for(N);
   constexpr int NT = 32 * W;
   constexpr int PERT = (32 * N + NT - 1) / NT;
-  constexpr int CH = RES ? (PERT < 4 ? PERT : 4) : (PERT < 8 ? PERT : 8);  // fewer staged voxels when x is staged too
+  constexpr int CH = row_chunk(PERT, RES ? 4 : 8);  // fewer staged voxels when x is staged too
   extern __shared__ float2 dyn[];
   float2 (*sm)[kPad] = tile_of<N>(dyn);
   __shared__ unsigned masks[3];
   __shared__ double red[32];
   if (a.state && a.state->done) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int j2 = a.subs[blockIdx.y];
+  const int j2 = a.subs[bk.y];
   const int off2 = a.g.ax[2].off[j2];
-  const RowTile rt = setup_rows(masks, a, off2);
-  float2* K = a.K;
-  for (int k0 = 0; k0 < PERT; k0 += CH) {
-    float2 kv[CH];
-#pragma unroll
-    for (int c = 0; c < CH; c++) {
-      int r, e;
-      kv[c] = make_float2(0.f, 0.f);
-      if (TileMap<N, NT>::at(tid, k0 + c, r, e) && rt.ok(r)) kv[c] = K[rt.base(r) + e];
-    }
-#pragma unroll
-    for (int c = 0; c < CH; c++) {
-      int r, e;
-      if (TileMap<N, NT>::at(tid, k0 + c, r, e)) sm[e][r] = kv[c];
-    }
-  }
-  if constexpr (N > 1) {
-    __syncthreads();
-    auto sld = [&](int e) { return sm[e][lane]; };
-    auto sst = [&](int e, float2 v) { sm[e][lane] = v; };
-    fft_run<N, W, true, false, 0, 1, true, true>(warp, lane, sm, a.tw, sld, sst);
-  }
-  __syncthreads();
+  const RowTile rt = setup_rows(masks, a, off2, j2, bk.x);
   // |r|^2 of this thread's (at most N/W) voxels in FP32, then FP64 across threads
   // and blocks: GB300's FP64 rate is too low for a per-voxel FP64 accumulation.
   float acc = 0.f;
-  const int mode = a.mode;
-  const float2* X = a.X;
-  const float2* __restrict__ B = a.B;
-  const bool need_x = mode != LAST_PLAIN;
-  const bool need_b = mode != LAST_PLAIN;
-  constexpr int CR = RES ? CH : 1;  // the residual form also stages x (high and low words)
-  for (int k0 = 0; k0 < PERT; k0 += CH) {
-    float2 xv[CH], bv[CH], sv[CR];
-    unsigned lv[CR];
+  if (rt.valid != 0u) {  // else every row lies in inactive subdomains: only the partial (zero) is stored
+    float2* K = a.K;
+    for (int k0 = 0; k0 < PERT; k0 += CH) {
+      float2 kv[CH];
 #pragma unroll
-    for (int c = 0; c < CH; c++) {
-      int r, e;
-      const bool ok = TileMap<N, NT>::at(tid, k0 + c, r, e);
-      xv[c] = make_float2(0.f, 0.f);
-      bv[c] = make_float2(0.f, 0.f);
-      if constexpr (RES) {
-        sv[c] = make_float2(0.f, 0.f);
-        lv[c] = 0u;
+      for (int c = 0; c < CH; c++) {
+        int r, e;
+        kv[c] = make_float2(0.f, 0.f);
+        if (TileMap<N, NT>::at(tid, k0 + c, r, e) && rt.ok(r)) kv[c] = K[rt.base(r) + e];
       }
-      if (ok) {
-        if (rt.ok(r)) {
-          const long long gi = rt.base(r) + e;
-          if (need_x) xv[c] = X[gi];
-          if (need_b) bv[c] = __ldg(B + gi);
-          if constexpr (RES) {
-            sv[c] = a.Xs[gi];
-            lv[c] = a.Xlo[gi];
-          }
-        }
+#pragma unroll
+      for (int c = 0; c < CH; c++) {
+        int r, e;
+        if (TileMap<N, NT>::at(tid, k0 + c, r, e)) sm[e][r] = kv[c];
       }
     }
+    if constexpr (N > 1) {
+      __syncthreads();
+      auto sld = [&](int e) { return sm[e][lane]; };
+      auto sst = [&](int e, float2 v) { sm[e][lane] = v; };
+      fft_run<N, W, true, false, 0, 1, true, true>(warp, lane, sm, a.tw, sld, sst);
+    }
+    __syncthreads();
+    const int mode = a.mode;
+    const float2* X = a.X;
+    const float2* __restrict__ B = a.B;
+    const bool need_x = mode != LAST_PLAIN;
+    const bool need_b = mode != LAST_PLAIN;
+    constexpr int CR = RES ? CH : 1;  // the residual form also stages x (high and low words)
+    for (int k0 = 0; k0 < PERT; k0 += CH) {
+      float2 xv[CH], bv[CH], sv[CR];
+      unsigned lv[CR];
 #pragma unroll
-    for (int c = 0; c < CH; c++) {
-      int r, e;
-      if (!TileMap<N, NT>::at(tid, k0 + c, r, e) || !rt.ok(r)) continue;
-      const long long gi = rt.base(r) + e;
-      const float2 w = sm[e][r];
-      if (mode == LAST_PLAIN) {
-        a.Xout[gi] = w;
-      } else if (mode == LAST_AOUT) {
-        a.Xout[gi] = cadd(w, cmul(make_float2(1.f - bv[c].x, -bv[c].y), xv[c]));
-      } else if (RES) {
+      for (int c = 0; c < CH; c++) {
+        int r, e;
+        const bool ok = TileMap<N, NT>::at(tid, k0 + c, r, e);
+        xv[c] = make_float2(0.f, 0.f);
+        bv[c] = make_float2(0.f, 0.f);
         if constexpr (RES) {
-          // residual form: xv = r'_n, e = r' - w, r'_{n+1} = r' - alpha (I - V) e,
-          // x_{n+1} = x_n - alpha r'_n; |r'_n|^2 of every voxel is summed here
-          acc = fmaf(xv[c].x, xv[c].x, fmaf(xv[c].y, xv[c].y, acc));
-          a.Xs[gi] = acc_update(sv[c], lv[c], make_float2(-a.alpha * xv[c].x, -a.alpha * xv[c].y));
-          a.Xlo[gi] = lv[c];
-          const float2 ee = csub(xv[c], w);
-          if (rt.lay(r) || in_layer2<N>(a, e)) {
-            a.E[gi] = ee;  // r' on the layers is finished by the layer update
-          } else {
-            const float2 rr = cmul(bv[c], ee);
-            a.Xout[gi] = make_float2(fmaf(-a.alpha, rr.x, xv[c].x), fmaf(-a.alpha, rr.y, xv[c].y));
+          sv[c] = make_float2(0.f, 0.f);
+          lv[c] = 0u;
+        }
+        if (ok) {
+          if (rt.ok(r)) {
+            const long long gi = rt.base(r) + e;
+            if (need_x) xv[c] = X[gi];
+            if (need_b) bv[c] = __ldg(B + gi);
+            if constexpr (RES) {
+              sv[c] = a.Xs[gi];
+              lv[c] = a.Xlo[gi];
+            }
           }
         }
-      } else {
-        const float2 ee = csub(xv[c], w);
-        if (rt.lay(r) || in_layer2<N>(a, e)) {
-          a.E[gi] = ee;  // finished by the layer update once all of e is known
+      }
+#pragma unroll
+      for (int c = 0; c < CH; c++) {
+        int r, e;
+        if (!TileMap<N, NT>::at(tid, k0 + c, r, e) || !rt.ok(r)) continue;
+        const long long gi = rt.base(r) + e;
+        const float2 w = sm[e][r];
+        if (mode == LAST_PLAIN) {
+          a.Xout[gi] = w;
+        } else if (mode == LAST_AOUT) {
+          a.Xout[gi] = cadd(w, cmul(make_float2(1.f - bv[c].x, -bv[c].y), xv[c]));
+        } else if (RES) {
+          if constexpr (RES) {
+            // residual form: xv = r'_n, e = r' - w, r'_{n+1} = r' - alpha (I - V) e,
+            // x_{n+1} = x_n - alpha r'_n; |r'_n|^2 of every voxel is summed here
+            acc = fmaf(xv[c].x, xv[c].x, fmaf(xv[c].y, xv[c].y, acc));
+            a.Xs[gi] = acc_update(sv[c], lv[c], make_float2(-a.alpha * xv[c].x, -a.alpha * xv[c].y));
+            a.Xlo[gi] = lv[c];
+            const float2 ee = csub(xv[c], w);
+            if (rt.lay(r) || in_layer2<N>(a, e)) {
+              a.E[gi] = ee;  // r' on the layers is finished by the layer update
+            } else {
+              const float2 rr = cmul(bv[c], ee);
+              a.Xout[gi] = make_float2(fmaf(-a.alpha, rr.x, xv[c].x), fmaf(-a.alpha, rr.y, xv[c].y));
+            }
+          }
         } else {
-          const float2 rr = cmul(bv[c], ee);
-          acc = fmaf(rr.x, rr.x, fmaf(rr.y, rr.y, acc));
-          a.Xout[gi] = (mode == LAST_ITER) ? make_float2(fmaf(-a.alpha, rr.x, xv[c].x), fmaf(-a.alpha, rr.y, xv[c].y))
-                                           : make_float2(-rr.x, -rr.y);
+          const float2 ee = csub(xv[c], w);
+          if (rt.lay(r) || in_layer2<N>(a, e)) {
+            a.E[gi] = ee;  // finished by the layer update once all of e is known
+          } else {
+            const float2 rr = cmul(bv[c], ee);
+            acc = fmaf(rr.x, rr.x, fmaf(rr.y, rr.y, acc));
+            a.Xout[gi] = (mode == LAST_ITER) ? make_float2(fmaf(-a.alpha, rr.x, xv[c].x), fmaf(-a.alpha, rr.y, xv[c].y))
+                                             : make_float2(-rr.x, -rr.y);
+          }
         }
       }
     }
   }
   if (a.partials) {
     const double s = block_sum((double)acc, red);
-    finish_block(Finish{a.partials, a.slot0, a.n_total, a.fin, a.hist}, s, red);
+    finish_block_at(Finish{a.partials, a.slot0, a.n_total, a.fin, a.hist}, s, red, bk.x + bk.nx * bk.y,
+                    bk.nx * bk.ny);
   }
+}
+
+template <int N, bool RES>
+__global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_last(const __grid_constant__ PassArgs a) {
+  rows_last_body<N, RES>(a, blk_here());
+}
+
+template <int N, bool RES>
+__global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_rows_last_batch(const PassArgs* __restrict__ d) {
+  __shared__ PassArgs a;
+  const PassArgs& ga = d[blockIdx.z];
+  const unsigned nx = row_blocks(ga), ny = (unsigned)ga.nsub;
+  if (blockIdx.x >= nx || blockIdx.y >= ny) return;
+  stage_args(&a, &ga);
+  rows_last_body<N, RES>(a, Blk{blockIdx.x, blockIdx.y, 0u, nx, ny});
 }
 
 // ---------------------------------------------------------------------------
 // Axis-1 / axis-0 transform of a tile of 32 consecutive axis-2 positions.
 // ---------------------------------------------------------------------------
+// bk: x the block of 32 axis-2 positions, y the index along the other axis
+// (i0 for AXIS 1, i1 for AXIS 0), z the subdomain slot.
 template <int N, int AXIS, bool INV>
-__global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_strided(const __grid_constant__ PassArgs a) {
+__device__ __forceinline__ void strided_body(const PassArgs& a, const Blk& bk) {
   constexpr int W = warps_for(N);
   extern __shared__ float2 dyn[];
   float2 (*sm)[kPad] = tile_of<N>(dyn);
   if (a.state && a.state->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j = a.subs[blockIdx.z];
-  const long long i2 = (long long)blockIdx.x * 32 + lane;
-  const bool valid = i2 < a.g.N2;
+  const int j = a.subs[bk.z];
+  const long long i2 = (long long)bk.x * 32 + lane;
+  bool valid = i2 < a.g.N2;
+  if (valid && a.active)
+    valid = AXIS == 1 ? sub_active(a.active, a.g, a.tb.sub[0][bk.y], j, a.tb.sub[2][i2])
+                      : sub_active(a.active, a.g, j, a.tb.sub[1][bk.y], a.tb.sub[2][i2]);
+  if (!__any_sync(0xffffffffu, valid)) return;  // the same 32 pencils in every warp
   long long base, stride;
   if (AXIS == 1) {
-    base = (long long)blockIdx.y * a.g.N1 * a.g.N2 + (long long)a.g.ax[1].off[j] * a.g.N2 + i2;
+    base = (long long)bk.y * a.g.N1 * a.g.N2 + (long long)a.g.ax[1].off[j] * a.g.N2 + i2;
     stride = a.g.N2;
   } else {
-    base = (long long)a.g.ax[0].off[j] * a.g.N1 * a.g.N2 + (long long)blockIdx.y * a.g.N2 + i2;
+    base = (long long)a.g.ax[0].off[j] * a.g.N1 * a.g.N2 + (long long)bk.y * a.g.N2 + i2;
     stride = a.g.N1 * a.g.N2;
   }
   float2* K = a.K;
@@ -466,6 +526,22 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_stride
     if (valid) K[base + e * stride] = v;
   };
   if constexpr (N > 1) fft_run<N, W, INV, false, 0, 1, false, false>(warp, lane, sm, a.tw, gld, gst);
+}
+
+template <int N, int AXIS, bool INV>
+__global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_strided(const __grid_constant__ PassArgs a) {
+  strided_body<N, AXIS, INV>(a, blk_here());
+}
+
+// Batched form: grid.y folds (index along the other axis, subdomain slot).
+template <int N, int AXIS, bool INV>
+__global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_strided_batch(const PassArgs* __restrict__ d) {
+  __shared__ PassArgs a;
+  const PassArgs& ga = d[blockIdx.z];
+  const unsigned gx = (unsigned)((ga.g.N2 + 31) / 32), ny = (unsigned)(AXIS == 1 ? ga.g.N0 : ga.g.N1);
+  if (blockIdx.x >= gx || blockIdx.y >= ny * (unsigned)ga.nsub) return;
+  stage_args(&a, &ga);
+  strided_body<N, AXIS, INV>(a, Blk{blockIdx.x, blockIdx.y % ny, blockIdx.y / ny, gx, ny});
 }
 
 // ---------------------------------------------------------------------------
@@ -479,15 +555,17 @@ struct MidPencil {
   const float* p20;
 };
 
-__device__ __forceinline__ MidPencil mid_pencil(const PassArgs& a) {
+// bk: x the block of 32 axis-2 positions, y the index i1, z the subdomain slot.
+__device__ __forceinline__ MidPencil mid_pencil(const PassArgs& a, const Blk& bk) {
   MidPencil m;
   const int lane = threadIdx.x & 31;
-  const int j = a.subs[blockIdx.z];
+  const int j = a.subs[bk.z];
   const int off0 = a.g.ax[0].off[j];
-  const long long i1 = blockIdx.y;
-  const long long i2 = (long long)blockIdx.x * 32 + lane;
+  const long long i1 = bk.y;
+  const long long i2 = (long long)bk.x * 32 + lane;
   m.valid = i2 < a.g.N2;
   const long long i2c = m.valid ? i2 : 0;
+  if (m.valid && a.active) m.valid = sub_active(a.active, a.g, j, a.tb.sub[1][i1], a.tb.sub[2][i2c]);
   m.base = (long long)off0 * a.g.N1 * a.g.N2 + i1 * a.g.N2 + i2;
   m.stride = a.g.N1 * a.g.N2;
   m.pl = a.tb.p2[1][i1] + a.tb.p2[2][i2c];
@@ -498,14 +576,15 @@ __device__ __forceinline__ MidPencil mid_pencil(const PassArgs& a) {
 
 // Propagator (L + I)^-1 = 1/(c(k0^2 - |p|^2) + 1) (Sec. 2) or the symbol of L,
 // c(k0^2 - |p|^2) (Eq. L-convolution), times 1/(n0 n1 n2).
-template <int N, int MIN_BLOCKS>
-__global__ void __launch_bounds__(32 * warps_for(N), MIN_BLOCKS) k_mid_turn(const __grid_constant__ PassArgs a) {
+template <int N>
+__device__ __forceinline__ void mid_turn_body(const PassArgs& a, const Blk& bk) {
   constexpr int W = warps_for(N);
   extern __shared__ float2 dyn[];
   float2 (*sm)[kPad] = tile_of<N>(dyn);
   if (a.state && a.state->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const MidPencil m = mid_pencil(a);
+  const MidPencil m = mid_pencil(a, bk);
+  if (!__any_sync(0xffffffffu, m.valid)) return;  // the same 32 pencils in every warp
   const float2 c = a.c, ck0 = a.ck0;
   float2* K = a.K;
   auto gld = [&](int e) { return m.valid ? K[m.base + e * m.stride] : make_float2(0.f, 0.f); };
@@ -531,6 +610,21 @@ __global__ void __launch_bounds__(32 * warps_for(N), MIN_BLOCKS) k_mid_turn(cons
   }
 }
 
+template <int N, int MIN_BLOCKS>
+__global__ void __launch_bounds__(32 * warps_for(N), MIN_BLOCKS) k_mid_turn(const __grid_constant__ PassArgs a) {
+  mid_turn_body<N>(a, blk_here());
+}
+
+template <int N, int MIN_BLOCKS>
+__global__ void __launch_bounds__(32 * warps_for(N), MIN_BLOCKS) k_mid_turn_batch(const PassArgs* __restrict__ d) {
+  __shared__ PassArgs a;
+  const PassArgs& ga = d[blockIdx.z];
+  const unsigned gx = (unsigned)((ga.g.N2 + 31) / 32), ny = (unsigned)ga.g.N1;
+  if (blockIdx.x >= gx || blockIdx.y >= ny * (unsigned)ga.nsub) return;
+  stage_args(&a, &ga);
+  mid_turn_body<N>(a, Blk{blockIdx.x, blockIdx.y % ny, blockIdx.y / ny, gx, ny});
+}
+
 // Forward-only (MID_FWD) or scaled inverse-only (MID_INV) axis-0 transform.
 template <int N>
 __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_mid_plain(const __grid_constant__ PassArgs a) {
@@ -539,7 +633,7 @@ __global__ void __launch_bounds__(32 * warps_for(N), fft_min_blocks(N)) k_mid_pl
   float2 (*sm)[kPad] = tile_of<N>(dyn);
   if (a.state && a.state->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const MidPencil m = mid_pencil(a);
+  const MidPencil m = mid_pencil(a, blk_here());
   float2* K = a.K;
   auto gst = [&](int e, float2 v) {
     if (m.valid) K[m.base + e * m.stride] = v;
@@ -671,6 +765,60 @@ cudaError_t run_size(int kind, int axis, bool inv, const PassArgs& a, int nrow_b
   return cudaGetLastError();
 }
 
+// Batched passes (several plans' passes of one edge in one launch, plan
+// blockIdx.z of d, grid sized for the largest plan): compiled for edges up to
+// kBatchMaxN. kind 0 first pass (tc: 8 for the t = 8 form of the fused axis-2
+// corrections), 1 last pass, 2 axis-1 pass, 3 axis-0 pass (forward, propagator,
+// inverse). smem: the largest dynamic shared memory of the plans.
+constexpr int kBatchMaxN = 128;
+
+template <int N>
+cudaError_t run_size_batch(int kind, bool inv, int tc, const PassArgs* d, dim3 grid, size_t smem, cudaStream_t st) {
+  if constexpr (N > kBatchMaxN) {
+    return cudaErrorInvalidValue;
+  } else {
+    const dim3 blk(32 * warps_for(N));
+    cudaError_t e = cudaSuccess;
+    switch (kind) {
+      case 0:
+        if (tc == 8) {
+          e = set_smem(k_rows_first_batch<N, 8>, smem);
+          if (e) return e;
+          k_rows_first_batch<N, 8><<<grid, blk, smem, st>>>(d);
+        } else {
+          e = set_smem(k_rows_first_batch<N, 0>, smem);
+          if (e) return e;
+          k_rows_first_batch<N, 0><<<grid, blk, smem, st>>>(d);
+        }
+        break;
+      case 1:
+        e = set_smem(k_rows_last_batch<N, false>, smem);
+        if (e) return e;
+        k_rows_last_batch<N, false><<<grid, blk, smem, st>>>(d);
+        break;
+      case 2:
+        if (inv) {
+          e = set_smem(k_strided_batch<N, 1, true>, smem);
+          if (e) return e;
+          k_strided_batch<N, 1, true><<<grid, blk, smem, st>>>(d);
+        } else {
+          e = set_smem(k_strided_batch<N, 1, false>, smem);
+          if (e) return e;
+          k_strided_batch<N, 1, false><<<grid, blk, smem, st>>>(d);
+        }
+        break;
+      case 3:
+        e = set_smem(k_mid_turn_batch<N, mid_min_blocks(N)>, smem);
+        if (e) return e;
+        k_mid_turn_batch<N, mid_min_blocks(N)><<<grid, blk, smem, st>>>(d);
+        break;
+      default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+}
+
 }  // namespace mbs
 
 // One case of a size-group switch (mbs_fft_group.cuh): launch the pass kernel
@@ -678,4 +826,8 @@ cudaError_t run_size(int kind, int axis, bool inv, const PassArgs& a, int nrow_b
 #define MBS_CASE(n) \
   case n:           \
     *err = mbs::run_size<n>(kind, axis, inv, a, nrb, st); \
+    return true;
+#define MBS_CASE_BATCH(n) \
+  case n:                 \
+    *err = mbs::run_size_batch<n>(kind, inv, tc, d, grid, smem, st); \
     return true;

@@ -67,10 +67,11 @@ struct Finish {
 };
 
 // Store this block's partial; the last block of the launch finishes the iteration.
-__device__ __forceinline__ void finish_block(const Finish& f, double block_total, double* red) {
+// b: this block's index among the nb blocks of its plan's launch (a batched launch
+// holds several plans' blocks; each plan counts its own).
+__device__ __forceinline__ void finish_block_at(const Finish& f, double block_total, double* red, unsigned b,
+                                                unsigned nb) {
   __shared__ unsigned int ticket;
-  const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
   if (threadIdx.x == 0) {
     f.partials[f.slot0 + b] = block_total;
     if (f.state) {
@@ -90,6 +91,11 @@ __device__ __forceinline__ void finish_block(const Finish& f, double block_total
     state_update(f.state, R, f.hist);
     f.state->ticket = 0u;
   }
+}
+
+__device__ __forceinline__ void finish_block(const Finish& f, double block_total, double* red) {
+  finish_block_at(f, block_total, red, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                  gridDim.x * gridDim.y * gridDim.z);
 }
 
 }  // namespace mbs

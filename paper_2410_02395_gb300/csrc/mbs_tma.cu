@@ -58,9 +58,10 @@ bool make_tma_map(CUtensorMap* tm, void* K, const GridDesc& g, int axis, int n) 
   return r == CUDA_SUCCESS;
 }
 
-// Persistent grid: as many CTAs as fit on the device at once (cached per kernel).
+// Persistent grid: as many CTAs as fit on the device at once (cached per
+// kernel), or `cap` per SM when the plan's tuner chose fewer.
 template <class Kern>
-static int persistent_blocks(Kern kernel, int threads, size_t smem, int ntiles) {
+static int persistent_blocks(Kern kernel, int threads, size_t smem, int ntiles, int cap) {
   static std::mutex mu;
   static std::unordered_map<const void*, int> cache;
   int per_sm = 0;
@@ -77,7 +78,9 @@ static int persistent_blocks(Kern kernel, int threads, size_t smem, int ntiles) 
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int b = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  if (per_sm < 1) per_sm = 1;
+  if (cap > 0 && cap < per_sm) per_sm = cap;
+  const int b = per_sm * (sms > 0 ? sms : 1);
   return ntiles < b ? ntiles : b;
 }
 
@@ -93,7 +96,7 @@ static cudaError_t run_tma(int kind, int axis, bool inv, const PassArgs& a, cons
 #define MBS_TMA_LAUNCH(KER)                                      \
   e = set_smem(KER, smem);                                       \
   if (e) return e;                                               \
-  KER<<<persistent_blocks(KER, threads, smem, ntiles), threads, smem, st>>>(a, tm);
+  KER<<<persistent_blocks(KER, threads, smem, ntiles, a.tma_ctas), threads, smem, st>>>(a, tm);
   if (kind == 3) {  // axis-0 pass: forward, multiplier, inverse
     if (axis != 0) return cudaErrorInvalidValue;
     MBS_TMA_LAUNCH((k_mid_tma<N>))
@@ -107,6 +110,35 @@ static cudaError_t run_tma(int kind, int axis, bool inv, const PassArgs& a, cons
   }
 #undef MBS_TMA_LAUNCH
   return cudaGetLastError();
+}
+
+// Resident CTAs per SM of the TMA-fed pass for edge n (0: no such kernel).
+int tma_max_ctas(int n, int kind) {
+  int per_sm = 0;
+  const int threads = 32 * warps_for(n);
+#define MBS_TMA_OCC(N)                                                                                        \
+  case N: {                                                                                                    \
+    const size_t smem = (size_t)2 * N * 32 * sizeof(float2);                                                   \
+    if (kind == 3) {                                                                                           \
+      if (set_smem(k_mid_tma<N>, smem) ||                                                                     \
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mid_tma<N>, threads, smem) != cudaSuccess)  \
+        per_sm = 0;                                                                                            \
+    } else {                                                                                                   \
+      if (set_smem(k_strided_tma<N, 1, false>, smem) ||                                                        \
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_strided_tma<N, 1, false>, threads, smem) !=  \
+              cudaSuccess)                                                                                     \
+        per_sm = 0;                                                                                            \
+    }                                                                                                          \
+    break;                                                                                                     \
+  }
+  switch (n) {
+    MBS_TMA_SIZES(MBS_TMA_OCC)
+    default:
+      break;
+  }
+#undef MBS_TMA_OCC
+  cudaGetLastError();
+  return per_sm;
 }
 
 cudaError_t launch_strided_tma(int n, int axis, bool inv, const PassArgs& a, const CUtensorMap& tm, cudaStream_t st) {

@@ -180,7 +180,11 @@ __global__ void __launch_bounds__(32 * warps_for(N), tma_min_blocks(N)) k_stride
   tma_tiles<N, AXIS>(a, &tm, dyn, bar, &ok, [&](float2 (*sm)[32], const TmaTile& tl) {
     const int j = a.subs[tl.js];
     const long long i2 = (long long)tl.ib * 32 + lane;
-    const bool valid = i2 < a.g.N2;
+    bool valid = i2 < a.g.N2;
+    if (valid && a.active)
+      valid = AXIS == 1 ? sub_active(a.active, a.g, a.tb.sub[0][tl.y], j, a.tb.sub[2][i2])
+                        : sub_active(a.active, a.g, j, a.tb.sub[1][tl.y], a.tb.sub[2][i2]);
+    if (!__any_sync(0xffffffffu, valid)) return;  // no pencil of this tile is active: nothing to store
     long long base, stride;
     if (AXIS == 1) {
       base = (long long)tl.y * a.g.N1 * a.g.N2 + (long long)a.g.ax[1].off[j] * a.g.N2 + i2;
@@ -220,8 +224,10 @@ __global__ void __launch_bounds__(32 * warps_for(N), tma_min_blocks(N)) k_mid_tm
     const int off0 = a.g.ax[0].off[j];
     const long long i1 = tl.y;
     const long long i2 = (long long)tl.ib * 32 + lane;
-    const bool valid = i2 < a.g.N2;
+    bool valid = i2 < a.g.N2;
     const long long i2c = valid ? i2 : 0;
+    if (valid && a.active) valid = sub_active(a.active, a.g, j, a.tb.sub[1][i1], a.tb.sub[2][i2c]);
+    if (!__any_sync(0xffffffffu, valid)) return;  // no pencil of this tile is active: nothing to store
     const long long base = (long long)off0 * a.g.N1 * a.g.N2 + i1 * a.g.N2 + i2;
     const long long stride = a.g.N1 * a.g.N2;
     const float pl = a.tb.p2[1][i1] + a.tb.p2[2][i2c];

@@ -98,3 +98,21 @@ def test_batched_solves_match_the_oracle(problems, form):
     b.close()
     for p in batched:
         p.close()
+
+
+def test_batch_of_x_form_plans_runs_fused(problems):
+    """The x-form plans with mixed-radix edges run as one launch per pass and edge
+    over all plans: far fewer launches per iteration than the plans' own."""
+    import paper_2410_02395_gb300 as pkg
+
+    plans = _plans(problems)
+    b = pkg.Batch(plans, graph_iters=10)
+    n, fused = b.launches_per_iteration()
+    assert fused
+    own = pkg.Batch(_plans(problems, corr_tf32=True), graph_iters=10)  # not fusable: each plan's launches
+    n_own, fused_own = own.launches_per_iteration()
+    assert not fused_own and n < n_own
+    own.close()
+    b.close()
+    for p in plans:
+        p.close()
