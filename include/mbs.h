@@ -354,6 +354,16 @@ MBS_API void mbs_batch_destroy(mbs_batch *batch);
 
 MBS_API void mbs_plan_destroy(mbs_plan *plan);
 
+/*
+ * 1 if this library was built with MBS_BOUNDS_CHECK: every kernel then checks
+ * the index range of its accesses to the grid arrays, skips an access outside
+ * the grid (nothing traps) and counts it in error words of the plan, and
+ * mbs_iterate, mbs_apply_operator and mbs_batch_iterate return MBS_EINVAL with
+ * the first offending site, index and limit in mbs_last_error(). 0 for the
+ * normal build, where the checks compile away.
+ */
+MBS_API int32_t mbs_build_checks_bounds(void);
+
 /* Thread-local description of the last error (empty string if none). */
 MBS_API const char *mbs_last_error(void);
 

@@ -52,11 +52,15 @@ class _Info(C.Structure):
 _lib = None
 
 
-def build(verbose=False):
-    """Compile the CUDA library in-tree (nvcc, sm_103a)."""
+def build(verbose=False, bounds_check=False):
+    """Compile the CUDA library in-tree (nvcc, sm_103a); bounds_check=True builds the
+    index-checking variant (``mbs_build_checks_bounds``) beside it."""
     from . import _build
 
-    return _build.build(verbose=verbose)
+    return _build.build(verbose=verbose, bounds_check=bounds_check)
+
+
+CHECKED_LIB_PATH = os.path.join(_HERE, "_lib", "libmbs_gb300_checked.so")
 
 
 def load_library(path=None):
@@ -96,6 +100,8 @@ def load_library(path=None):
     lib.mbs_plan_destroy.restype = None
     lib.mbs_last_error.argtypes = []
     lib.mbs_last_error.restype = C.c_char_p
+    lib.mbs_build_checks_bounds.argtypes = []
+    lib.mbs_build_checks_bounds.restype = C.c_int32
     for name in ("mbs_plan_create", "mbs_workspace_bytes", "mbs_plan_get_info", "mbs_apply_operator",
                  "mbs_set_source", "mbs_set_initial_field", "mbs_get_active_subdomains", "mbs_iterate", "mbs_get_field", "mbs_get_history", "mbs_solve",
                  "mbs_profile_iterations", "mbs_batch_create", "mbs_batch_iterate"):
@@ -167,8 +173,8 @@ class Plan:
                  split_sizes=None, graph_iters=0, no_graph=False, corr_tf32=False, residual_form=False,
                  no_tma=False, force_tma=False, plain_steps=False, activation=False, activation_threshold=0.0,
                  no_tune=False,
-                 tma_wait_cycles=0, stream=None, workspace=None):
-        self.lib = load_library()
+                 tma_wait_cycles=0, stream=None, workspace=None, library=None):
+        self.lib = library if library is not None else load_library()
         self.shape = tuple(int(s) for s in shape)
         opts = _Options()
         self.lib.mbs_default_options(C.byref(opts))

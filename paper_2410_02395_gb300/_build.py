@@ -2,7 +2,9 @@
 
 Every ``csrc/*.cu`` file is compiled to an object in ``_build/`` in parallel,
 then linked into ``_lib/libmbs_gb300.so``. Objects are rebuilt when their source
-or any header is newer.
+or any header is newer. ``bounds_check=True`` builds the index-checking variant
+(``-DMBS_BOUNDS_CHECK``) into ``_build_checked/`` and
+``_lib/libmbs_gb300_checked.so``.
 """
 from __future__ import annotations
 
@@ -18,6 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libmbs_gb300.so")
+LIB_CHECKED = os.path.join(LIBDIR, "libmbs_gb300_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
@@ -43,24 +46,27 @@ def _stale(obj, src, hdr_mtime):
     return os.path.getmtime(src) > m or hdr_mtime > m
 
 
-def build(verbose=False, jobs=None):
+def build(verbose=False, jobs=None, bounds_check=False):
     """Compile and link the library; returns the path of the shared object."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = BUILD + "_checked" if bounds_check else BUILD
+    lib = LIB_CHECKED if bounds_check else LIB
+    flags = FLAGS + (["-DMBS_BOUNDS_CHECK"] if bounds_check else [])
+    os.makedirs(build_dir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_mtime = max([os.path.getmtime(h) for h in _headers()] + [0.0])
     objs = []
     todo = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.splitext(os.path.basename(s))[0] + ".o")
+        o = os.path.join(build_dir, os.path.splitext(os.path.basename(s))[0] + ".o")
         objs.append(o)
         if _stale(o, s, hdr_mtime):
             todo.append((s, o))
 
     def compile_one(so):
         s, o = so
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", s, "-o", o]
+        cmd = [nvcc] + ARCH + flags + ["-c", s, "-o", o]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (s, r.stdout, r.stderr))
@@ -73,13 +79,13 @@ def build(verbose=False, jobs=None):
     if todo:
         with cf.ThreadPoolExecutor(max_workers=nj) as ex:
             list(ex.map(compile_one, todo))
-    if todo or not os.path.exists(LIB):
-        cmd = [nvcc] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs
+    if todo or not os.path.exists(lib):
+        cmd = [nvcc] + ARCH + ["-shared", "-o", lib + ".tmp"] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+        os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":

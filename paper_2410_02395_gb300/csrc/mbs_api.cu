@@ -170,6 +170,7 @@ struct mbs_plan {
   int n_rows_partials, n_shell_partials;
   DevState* state;
   DevState* free_state;  // never marked done (operator applications)
+  unsigned long long* bounds_err;  // error words of the index-checking build (see GridDesc::err)
   double* history;
   int* box_dev;
   double* host_pinned;  // plain form: kPlainBlocks partial sums read back every iteration
@@ -264,6 +265,7 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
   char* pfst = take(sizeof(DevState));
   char* phist = take(kHistCap * sizeof(double));
   char* pbox = take(6 * sizeof(int));
+  char* perr = take(4 * sizeof(unsigned long long));
   const int nsub = p->S[0] * p->S[1] * p->S[2];
   const bool act = (p->flags & MBS_FLAG_ACTIVATION) != 0;
   char* pact = act ? take(nsub * sizeof(int)) : nullptr;
@@ -305,6 +307,8 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
     p->free_state = (DevState*)pfst;
     p->history = (double*)phist;
     p->box_dev = (int*)pbox;
+    p->bounds_err = (unsigned long long*)perr;
+    p->g.err = p->bounds_err;
     p->act_dev = (int*)pact;
     p->act_norms = (double*)pactn;
     p->act_faces = (ActFace*)pactf;
@@ -734,7 +738,7 @@ cudaError_t mid_pass(const mbs_plan* p, const PassArgs& a, int n) {
 // the defaults: TMA feed wherever a tensor map exists with as many CTAs as fit,
 // side-split correction kernels of 128 threads.
 // ---------------------------------------------------------------------------
-const char* kTuneBuild = "tune-v2 " __DATE__ " " __TIME__;
+const char* kTuneBuild = "tune-v3 " __DATE__ " " __TIME__;
 
 std::string tune_cache_path() {
   const char* e = getenv("MBS_TUNE_CACHE");
@@ -790,35 +794,36 @@ std::string tune_key(const mbs_plan* p, const char* kind, int n) {
   return std::string(buf);
 }
 
-// Fastest of `count` candidates: a warm-up launch of each, then three rounds
-// alternating the candidates, three timed launches per candidate and round,
-// the fastest round counting. Before every timed launch the L2 is flushed by
-// writing `flush` (256 MB, if given): inside the iteration a pass finds its
-// data in HBM, while back-to-back launches on a grid of about the L2's size
-// would find much of it cached and favour the wrong shape.
-constexpr long long kFlushElems = 32ll << 20;  // float2: 256 MB
-mbs_status time_candidates(mbs_plan* p, int count, const std::function<cudaError_t(int)>& launch, float2* flush,
-                           int* best_out) {
+cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec);
+
+// Fastest of `count` launch configurations, timed by whole iterations of the
+// plan: apply(v) sets configuration v, then one warm-up iteration of each, then
+// three rounds alternating the configurations, two timed iterations (CUDA
+// events) per configuration and round, the fastest round counting. Whole
+// iterations are timed because a pass's speed depends on what the previous
+// pass left in L2: timings of isolated, repeated launches picked shapes that
+// were slower inside the iteration. The plan's state is armed for the timing
+// (no stop) and reset afterwards by the caller.
+mbs_status time_configs(mbs_plan* p, int count, const std::function<void(int)>& apply, int* best_out) {
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   std::vector<float> best(count, 1e30f);
   mbs_status st = MBS_OK;
-  for (int v = 0; v < count && !st; v++)
-    if (launch(v)) st = fail(MBS_ECUDA, "tuning launch failed");
+  for (int v = 0; v < count && !st; v++) {
+    apply(v);
+    if (enqueue_iteration(p, nullptr)) st = fail(MBS_ECUDA, "tuning launch failed");
+  }
   for (int round = 0; round < 3 && !st; round++)
     for (int v = 0; v < count && !st; v++) {
-      float tot = 0.f;
-      for (int r = 0; r < 3 && !st; r++) {
-        float ms = 0.f;
-        if (flush && launch_zero(flush, kFlushElems, p->stream)) st = fail(MBS_ECUDA, "tuning flush failed");
-        if (!st && cudaEventRecord(e0, p->stream)) st = fail(MBS_ECUDA, "tuning event failed");
-        if (!st && launch(v)) st = fail(MBS_ECUDA, "tuning launch failed");
-        if (!st && (cudaEventRecord(e1, p->stream) || cudaEventSynchronize(e1) || cudaEventElapsedTime(&ms, e0, e1)))
-          st = fail(MBS_ECUDA, "tuning event failed");
-        tot += ms;
-      }
-      if (!st) best[v] = std::min(best[v], tot);
+      apply(v);
+      float ms = 0.f;
+      if (cudaEventRecord(e0, p->stream)) st = fail(MBS_ECUDA, "tuning event failed");
+      for (int r = 0; r < 2 && !st; r++)
+        if (enqueue_iteration(p, nullptr)) st = fail(MBS_ECUDA, "tuning launch failed");
+      if (!st && (cudaEventRecord(e1, p->stream) || cudaEventSynchronize(e1) || cudaEventElapsedTime(&ms, e0, e1)))
+        st = fail(MBS_ECUDA, "tuning event failed");
+      if (!st) best[v] = std::min(best[v], ms);
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -827,97 +832,101 @@ mbs_status time_candidates(mbs_plan* p, int count, const std::function<cudaError
   return MBS_OK;
 }
 
-mbs_status tune_plan_with(mbs_plan* p, float2* flush);
-
 mbs_status tune_plan(mbs_plan* p) {
   NvtxRange nvtx_("mbs tuner");
-  float2* flush = nullptr;  // released again below; without it the timing runs unflushed
-  if (cudaMalloc((void**)&flush, kFlushElems * sizeof(float2)) != cudaSuccess) {
-    cudaGetLastError();
-    flush = nullptr;
-  }
-  const mbs_status st = tune_plan_with(p, flush);
-  if (flush) cudaFree(flush);
-  return st;
-}
-
-mbs_status tune_plan_with(mbs_plan* p, float2* flush) {
   const bool fixed = (p->flags & (MBS_FLAG_NO_TUNE | MBS_FLAG_FORCE_TMA)) != 0;
   const std::string path = tune_cache_path();
   int timed = 0, cached = 0;
   std::string summary;
-  PassArgs a = base_args(p);
-  a.state = p->free_state;
-  a.tma_wait = 0;  // the full bound: a caller's short bound is for the iteration and the operators
-  a.mode = MID_PROP;
-  // axis-1 passes: candidate 0 register-fed, c >= 1 TMA-fed with c CTAs per SM
-  std::vector<int> drop;
-  for (auto& gy : p->groups[1]) {
-    auto it = p->tmaps.find(1 * 65536 + gy.n);
-    if (it == p->tmaps.end()) continue;
-    int choice = 0;  // TMA, as many CTAs as fit
-    if (!fixed) {
-      const std::string key = tune_key(p, "axis1", gy.n);
-      const std::string val = tune_cache_get(path, key);
-      if (!val.empty()) {
-        choice = atoi(val.c_str());
-        cached++;
-      } else {
-        const int m = std::max(1, tma_max_ctas(gy.n, 2));
-        a.nsub = gy.nsub;
-        memcpy(a.subs, gy.subs, sizeof(a.subs));
-        set_len_tables(p, a, gy.n);
-        int best = 0;
-        mbs_status st = time_candidates(p, m + 1, [&](int v) -> cudaError_t {
-          if (v == 0) {
-            cudaError_t e = launch_strided(gy.n, 1, false, a, p->stream);
-            return e ? e : launch_strided(gy.n, 1, true, a, p->stream);
-          }
-          PassArgs b = a;
-          b.tma_ctas = v;
-          cudaError_t e = launch_strided_tma(gy.n, 1, false, b, it->second, p->stream);
-          return e ? e : launch_strided_tma(gy.n, 1, true, b, it->second, p->stream);
-        }, flush, &best);
-        if (st) return st;
-        choice = best == 0 ? -1 : best;  // -1: register-fed
-        tune_cache_put(path, key, std::to_string(choice));
-        timed++;
-      }
-    }
-    if (choice < 0) {
-      drop.push_back(it->first);
-    } else {
-      p->tma_ctas[gy.n] = choice;
-    }
-    summary += "axis1/" + std::to_string(gy.n) + ":" +
-               (choice < 0 ? std::string("reg") : "tma" + (choice > 0 ? "x" + std::to_string(choice) : std::string())) +
-               " ";
-  }
-  for (int k : drop) p->tmaps.erase(k);
-  // FP32 correction kernels of axes 0 and 1 (both launches of the iteration's x corrections)
   p->corr_variant = 0;
   p->corr_block = 128;
   const bool corr01 = p->has_shell && (p->a[0] > 0 || p->a[1] > 0) && !(p->flags & MBS_FLAG_CORR_TF32);
+  // what is left to time, with the keys of the cache
+  struct Axis1 {
+    int n;
+    CUtensorMap tm;
+    std::string key;
+    int choice;  // -1 register-fed, c >= 1 TMA-fed with c CTAs per SM, 0 TMA with as many as fit
+    bool todo;
+  };
+  std::vector<Axis1> ax1;
+  for (auto& gy : p->groups[1]) {
+    auto it = p->tmaps.find(1 * 65536 + gy.n);
+    if (it == p->tmaps.end()) continue;
+    Axis1 g1{gy.n, it->second, tune_key(p, "axis1", gy.n), 0, false};
+    if (!fixed) {
+      const std::string val = tune_cache_get(path, g1.key);
+      if (!val.empty()) {
+        g1.choice = atoi(val.c_str());
+        cached++;
+      } else {
+        g1.todo = true;
+      }
+    }
+    ax1.push_back(g1);
+  }
+  const std::string ckey = tune_key(p, "corr01", 0);
+  int cchoice = 0;
+  bool ctodo = false;
   if (corr01 && !fixed) {
-    const std::string key = tune_key(p, "corr01", 0);
-    const std::string val = tune_cache_get(path, key);
-    int choice = 0;
+    const std::string val = tune_cache_get(path, ckey);
     if (!val.empty()) {
-      choice = atoi(val.c_str());
+      cchoice = atoi(val.c_str());
       cached++;
     } else {
-      mbs_status st = time_candidates(p, 4, [&](int v) -> cudaError_t {
-        p->corr_variant = v / 2;
-        p->corr_block = (v % 2) ? 64 : 128;
-        return run_corr(p, p->x, p->K, p->free_state, false);
-      }, flush, &choice);
+      ctodo = true;
+    }
+  }
+  auto apply_axis1 = [&](const Axis1& g1, int choice) {
+    const int key = 1 * 65536 + g1.n;
+    if (choice < 0) {
+      p->tmaps.erase(key);
+    } else {
+      p->tmaps[key] = g1.tm;
+      p->tma_ctas[g1.n] = choice;
+    }
+  };
+  for (auto& g1 : ax1) apply_axis1(g1, g1.choice);
+  p->corr_variant = cchoice / 2;
+  p->corr_block = (cchoice % 2) ? 64 : 128;
+  bool any_todo = ctodo;
+  for (auto& g1 : ax1) any_todo = any_todo || g1.todo;
+  if (any_todo) {
+    CU(launch_state_arm(p->state, 1 << 30, 0.0, 1, kHistCap, p->stream));  // no stop while timing
+    if (p->resform) {  // the residual form iterates on r' (x and its low word are zero already)
+      CU(launch_zero(p->r, nvox(p), p->stream));
+      CU(cudaMemsetAsync(p->xlo, 0, nvox(p) * sizeof(unsigned), p->stream));
+    }
+    for (auto& g1 : ax1) {  // one axis-1 edge group at a time, the others as chosen so far
+      if (!g1.todo) continue;
+      const int m = std::max(1, tma_max_ctas(g1.n, 2));
+      int best = 0;  // candidate 0 register-fed, c TMA-fed with c CTAs per SM
+      mbs_status st = time_configs(p, m + 1, [&](int v) { apply_axis1(g1, v == 0 ? -1 : v); }, &best);
       if (st) return st;
-      tune_cache_put(path, key, std::to_string(choice));
+      g1.choice = best == 0 ? -1 : (best == m ? 0 : best);
+      apply_axis1(g1, g1.choice);
+      tune_cache_put(path, g1.key, std::to_string(g1.choice));
       timed++;
     }
-    p->corr_variant = choice / 2;
-    p->corr_block = (choice % 2) ? 64 : 128;
+    if (ctodo) {
+      mbs_status st = time_configs(p, 4, [&](int v) {
+        p->corr_variant = v / 2;
+        p->corr_block = (v % 2) ? 64 : 128;
+      }, &cchoice);
+      if (st) return st;
+      p->corr_variant = cchoice / 2;
+      p->corr_block = (cchoice % 2) ? 64 : 128;
+      tune_cache_put(path, ckey, std::to_string(cchoice));
+      timed++;
+    }
+    CU(launch_zero(p->x, nvox(p), p->stream));  // the timing iterations left their field
+    CU(launch_state_arm(p->state, 0, 0.0, 1, kHistCap, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
   }
+  for (auto& g1 : ax1)
+    summary += "axis1/" + std::to_string(g1.n) + ":" +
+               (g1.choice < 0 ? std::string("reg") : "tma" + (g1.choice > 0 ? "x" + std::to_string(g1.choice)
+                                                                             : std::string())) + " ";
   if (corr01)
     summary += std::string("corr01:") + (p->corr_variant ? "pencil" : "side") + "/" + std::to_string(p->corr_block);
   p->tune_source = fixed ? 0 : (timed > 0 ? 1 : (cached > 0 ? 2 : 0));
@@ -1347,6 +1356,25 @@ mbs_status check_free_state(mbs_plan* p) {
   return MBS_OK;
 }
 
+// The index-checking build (MBS_BOUNDS_CHECK): report and clear the error words
+// the kernels wrote. A no-op in the normal build.
+mbs_status check_bounds(mbs_plan* p, mbs_status st) {
+#ifdef MBS_BOUNDS_CHECK
+  unsigned long long w[4] = {0, 0, 0, 0};
+  if (cudaMemcpy(w, p->bounds_err, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(MBS_ECUDA, "reading the index-check words failed");
+  if (w[0]) {
+    cudaMemset(p->bounds_err, 0, sizeof(w));
+    return fail(MBS_EINVAL, "index out of range: " + std::to_string(w[0]) + " accesses skipped, the first at site " +
+                                std::to_string(w[1]) + ", index " + std::to_string((long long)w[2]) + ", limit " +
+                                std::to_string(w[3]));
+  }
+#else
+  (void)p;
+#endif
+  return st;
+}
+
 }  // namespace
 
 bool mbs_plan_corr_view(const mbs_plan* p, CorrView* v) {
@@ -1468,6 +1496,8 @@ mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double p
     p->own_base = true;
   }
   layout(p, (char*)p->base, true);
+  if (cudaMemsetAsync(p->bounds_err, 0, 4 * sizeof(unsigned long long), p->stream) != cudaSuccess)
+    return cleanup(fail(MBS_ECUDA, "zero fill failed"));
   if (cudaMallocHost((void**)&p->host_state, sizeof(DevState)) != cudaSuccess)
     return cleanup(fail(MBS_ECUDA, "pinned allocation failed"));
   st = upload_tables(p);
@@ -1506,6 +1536,14 @@ mbs_status mbs_plan_create(mbs_plan** plan_out, const int64_t shape[3], double p
   if (clear_free_state(p)) return cleanup(fail(MBS_ECUDA, "state init failed"));
   *plan_out = p;
   return MBS_OK;
+}
+
+int32_t mbs_build_checks_bounds(void) {
+#ifdef MBS_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
 }
 
 mbs_status mbs_plan_get_info(const mbs_plan* p, mbs_plan_info* info) {
@@ -1635,7 +1673,7 @@ mbs_status mbs_apply_operator(mbs_plan* p, int32_t which, const void* x, void* o
   if (e) return fail(MBS_ECUDA, std::string("operator launch: ") + cudaGetErrorString(e));
   if (!out_dev) CU(cudaMemcpyAsync(out, od, nv * sizeof(float2), cudaMemcpyDeviceToHost, p->stream));
   CU(cudaStreamSynchronize(p->stream));
-  return check_free_state(p);
+  return check_bounds(p, check_free_state(p));
 }
 
 mbs_status mbs_set_source(mbs_plan* p, const void* source) {
@@ -1810,6 +1848,8 @@ restart:
   }
   if (iters_done) *iters_done = hs.iter;
   if (residual) *residual = hs.eps;
+  st = check_bounds(p, MBS_OK);
+  if (st) return st;
   if (hs.status == MBS_ENAN) return fail(MBS_ENAN, "residual is not finite");
   if (hs.status == MBS_EDIVERGE) return fail(MBS_EDIVERGE, "residual kept rising");
   if (hs.status == MBS_ETIMEOUT) return fail(MBS_ETIMEOUT, "a bounded wait for a tensor-map copy expired");
@@ -2307,6 +2347,10 @@ mbs_status mbs_batch_iterate(mbs_batch* b, int32_t n_iter, double tol, int32_t n
   mbs_status st = batch_read_states(b);
   if (st) return st;
   mbs_status worst = MBS_OK;
+  for (mbs_plan* p : b->plans) {
+    st = check_bounds(p, MBS_OK);  // the index-checking build only
+    if (st) return st;
+  }
   for (size_t i = 0; i < b->plans.size(); i++) {
     const DevState& hs = b->host_states[i];
     mbs_status si = hs.status ? (mbs_status)hs.status : (hs.iter > 0 && hs.eps < tol ? MBS_OK : MBS_ENOCONV);

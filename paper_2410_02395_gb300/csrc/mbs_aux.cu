@@ -66,6 +66,8 @@ __global__ void __launch_bounds__(128) k_corr_strided(const __grid_constant__ Co
   }
   const int off = ax.off[s], n = ax.n[s];
   const int L = ax.left[s], R = ax.right[s];
+  // the pencil along the whole axis covers the own subdomain and both neighbours
+  if (!grid_range_ok(a.g, base, base + (long long)(ax.N - 1) * stride, BC_CORR)) return;
   const float2* __restrict__ F = a.F;
   float2 D[T], E[T];
 #pragma unroll
@@ -144,6 +146,7 @@ __device__ __forceinline__ void corr_side_body(const CorrArgs& a, long long gid)
   const int nb = side ? ax.right[s] : ax.left[s];
   const long long own0 = base + (long long)(side ? off : off + n - T) * stride;
   const long long nb0 = nb >= 0 ? base + (long long)(side ? ax.off[nb] : ax.off[nb] + ax.n[nb] - T) * stride : 0;
+  if (!grid_range_ok(a.g, base, base + (long long)(ax.N - 1) * stride, BC_CORR)) return;  // the whole pencil
   const float2* __restrict__ F = a.F;
   float2 G[T];
 #pragma unroll
@@ -208,6 +211,7 @@ __global__ void __launch_bounds__(256) k_corr_rows(const __grid_constant__ CorrA
     const long long i0 = rho / N1, i1 = rho - i0 * N1;
     const bool add = a.tb.shell[0][i0] || a.tb.shell[1][i1];
     const long long rb = rho * N2;
+    if (!grid_range_ok(a.g, rb, rb + N2 - 1, BC_CORR)) continue;  // the warp's row
     for (int idx = lane; idx < M; idx += 32) {
       const int s = idx / (2 * T), k = idx - s * 2 * T;
       const int q = k < T ? k : ax.n[s] - T + (k - T);
@@ -301,7 +305,7 @@ __global__ void __launch_bounds__(128) k_corr_tc(const __grid_constant__ CorrArg
   const int ss = (int)(wid / ngroups);
   const int s = ss >> 1, side = ss & 1;
   const long long p = (wid - (long long)ss * ngroups) * 32 + lane;
-  const bool valid = p < npen;
+  bool valid = p < npen;
   long long base = 0, stride;
   bool add = false;
   if (d == 0) {
@@ -322,6 +326,7 @@ __global__ void __launch_bounds__(128) k_corr_tc(const __grid_constant__ CorrArg
   const int nb = side ? ax.right[s] : ax.left[s];
   const long long own0 = base + (long long)(side ? off : off + n - t) * stride;
   const long long nb0 = nb >= 0 ? base + (long long)(side ? ax.off[nb] : ax.off[nb] + ax.n[nb] - t) * stride : 0;
+  if (valid) valid = grid_range_ok(a.g, base, base + (long long)(ax.N - 1) * stride, BC_CORR);  // the pencil
   // gather g = f_neighbour - f_own into the warp's A rows 2*lane, 2*lane+1
   for (int b = 0; b < TP; b++) {
     float2 g = make_float2(0.f, 0.f);
@@ -447,6 +452,7 @@ __global__ void __launch_bounds__(128) k_corr_generic(const __grid_constant__ Co
   }
   const int off = ax.off[s], n = ax.n[s];
   const int L = ax.left[s], R = ax.right[s];
+  if (!grid_range_ok(a.g, base, base + (long long)(ax.N - 1) * stride, BC_CORR)) return;  // the whole pencil
   const float2* __restrict__ F = a.F;
   float2* C = a.C;
   auto at = [&](int pos) { return F[base + (long long)pos * stride]; };
@@ -624,6 +630,7 @@ __global__ void __launch_bounds__(256, 4) k_shell(const __grid_constant__ ShellA
       i1 = a.tb.l1[q - (q / a.tb.nl1) * a.tb.nl1];
     }
     const long long rb = (i0 * a.g.N1 + i1) * N2;
+    if (!grid_range_ok(a.g, rb, rb + N2 - 1, BC_SHELL)) continue;  // the warp's row
     for (long long k0 = 0; k0 < N2; k0 += 32 * U) {
       long long v[U];
 #pragma unroll
@@ -662,6 +669,7 @@ __global__ void __launch_bounds__(256, 4) k_shell(const __grid_constant__ ShellA
           i1 = a.tb.c1[row - (row / nc1) * nc1];
         }
         v[u] = (i0 * a.g.N1 + i1) * N2 + a.tb.sh2list[k];
+        if (!grid_range_ok(a.g, v[u], v[u], BC_SHELL)) v[u] = -1;
       }
     }
     acc += (double)shell_batch<U, MODE>(a, v);
@@ -757,6 +765,7 @@ __device__ __forceinline__ void shell_rows_body(const ShellArgs& a, unsigned bx,
         i1 = (unsigned)a.tb.l1[q - (q / nl1) * nl1];
       }
       const long long rb = ((long long)i0 * N1 + i1) * (long long)n2;
+      if (!grid_range_ok(a.g, rb, rb + n2 - 1, BC_SHELL)) continue;  // the warp's row
       const float2* Cr = a.C + rb;
       const float2* Er = a.E + rb;
       const float2* __restrict__ Br = a.B + rb;
@@ -812,6 +821,7 @@ __device__ __forceinline__ void shell_rows_body(const ShellArgs& a, unsigned bx,
       const int r00 = a.active ? a.tb.sub[0][i00] : 0, r10 = a.active ? a.tb.sub[1][i10] : 0;
       const int r01 = a.active && live1 ? a.tb.sub[0][i01] : 0, r11 = a.active && live1 ? a.tb.sub[1][i11] : 0;
       const long long rb0 = (long long)rho0 * n2, rb1 = (long long)rho1 * n2;
+      if (!grid_range_ok(a.g, rb0, (live1 ? rb1 : rb0) + n2 - 1, BC_SHELL)) continue;  // the warp's two rows
       float2 e0[J], b0[J], x0[J], c0[J], e1[J], b1[J], x1[J], c1[J];
 #pragma unroll
       for (int j = 0; j < J; j++) {
@@ -989,6 +999,7 @@ __global__ void __launch_bounds__(256) k_act_norms(const float2* __restrict__ X,
        pp += (long long)gridDim.x * blockDim.x) {
     const long long ia = pp / nb, ib = pp - ia * nb;
     const long long base = org + ia * st[da] + ib * st[db] + l0;
+    if (!grid_range_ok(g, base, base + (long long)(t - 1) * st[d], BC_CORR)) continue;
     for (int q = 0; q < t; q++) {
       float vx = 0.f, vy = 0.f;
       for (int b = 0; b < t; b++) {
@@ -1030,6 +1041,7 @@ __global__ void __launch_bounds__(256) k_plain_step(const __grid_constant__ Plai
     const bool lay01 = a.tb.shell[0][i0] | a.tb.shell[1][i1];
     const bool srow = a.S && i0 >= a.sbox[0] && i0 < a.sbox[1] && i1 >= a.sbox[2] && i1 < a.sbox[3];
     const long long rb = rho * N2;
+    if (!grid_range_ok(a.g, rb, rb + N2 - 1, BC_PLAIN)) continue;  // the block's row
     float racc = 0.f;
     for (long long i2 = threadIdx.x; i2 < N2; i2 += blockDim.x) {
       const long long v = rb + i2;

@@ -27,7 +27,13 @@ struct GridDesc {
   int64_t N0, N1, N2;
   int t;
   AxisDesc ax[3];
+  // index checking build (MBS_BOUNDS_CHECK): error words {count, site, index,
+  // limit} of the first out-of-range access; unused otherwise
+  unsigned long long* err;
 };
+
+// Sites of the index checks (the second error word).
+enum BoundsSite { BC_ROWS = 1, BC_STRIDED = 2, BC_MID = 3, BC_TMA = 4, BC_CORR = 5, BC_SHELL = 6, BC_PLAIN = 7 };
 
 // Per-axis tables over the global index along that axis.
 struct AxisTables {
@@ -173,6 +179,29 @@ constexpr int kPlainBlocks = 152 * 8;
 cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t st);
 
 #ifdef __CUDACC__
+// Index check of an access range [lo, hi] of a grid array. In the build with
+// MBS_BOUNDS_CHECK an index outside [0, N0 N1 N2) counts an error in g.err
+// (the first one also stores its site, index and limit) and the caller skips
+// the access; nothing traps. In the normal build it is always true.
+__device__ __forceinline__ bool grid_range_ok(const GridDesc& g, long long lo, long long hi, int site) {
+#ifdef MBS_BOUNDS_CHECK
+  const long long lim = g.N0 * g.N1 * g.N2;
+  if (lo >= 0 && hi < lim && lo <= hi) return true;
+  if (g.err && atomicAdd(g.err, 1ull) == 0ull) {
+    g.err[1] = (unsigned long long)site;
+    g.err[2] = (unsigned long long)(lo < 0 ? lo : hi);
+    g.err[3] = (unsigned long long)lim;
+  }
+  return false;
+#else
+  (void)g;
+  (void)lo;
+  (void)hi;
+  (void)site;
+  return true;
+#endif
+}
+
 // Subdomain activation (Sec. 3.1, "Implementation"): with flags, subdomain
 // (j0, j1, j2) is computed only while act[(j0 S1 + j1) S2 + j2] is set; the
 // field of an inactive subdomain stays zero.

@@ -110,7 +110,8 @@ __device__ __forceinline__ RowTile setup_rows(unsigned* masks, const PassArgs& a
     bool v = false, l = false, sr = false;
     if (rho < rows) {
       const long long i0 = rho / a.g.N1, i1 = rho - i0 * a.g.N1;
-      v = sub_active(a.active, a.g, a.tb.sub[0][i0], a.tb.sub[1][i1], j2);
+      v = sub_active(a.active, a.g, a.tb.sub[0][i0], a.tb.sub[1][i1], j2) &&
+          grid_range_ok(a.g, rho * a.g.N2, rho * a.g.N2 + a.g.N2 - 1, BC_ROWS);  // the row's voxels
       l = a.tb.shell[0][i0] | a.tb.shell[1][i1];
       sr = a.S && i0 >= a.sbox[0] && i0 < a.sbox[1] && i1 >= a.sbox[2] && i1 < a.sbox[3];
     }
@@ -511,7 +512,6 @@ __device__ __forceinline__ void strided_body(const PassArgs& a, const Blk& bk) {
   if (valid && a.active)
     valid = AXIS == 1 ? sub_active(a.active, a.g, a.tb.sub[0][bk.y], j, a.tb.sub[2][i2])
                       : sub_active(a.active, a.g, j, a.tb.sub[1][bk.y], a.tb.sub[2][i2]);
-  if (!__any_sync(0xffffffffu, valid)) return;  // the same 32 pencils in every warp
   long long base, stride;
   if (AXIS == 1) {
     base = (long long)bk.y * a.g.N1 * a.g.N2 + (long long)a.g.ax[1].off[j] * a.g.N2 + i2;
@@ -520,6 +520,8 @@ __device__ __forceinline__ void strided_body(const PassArgs& a, const Blk& bk) {
     base = (long long)a.g.ax[0].off[j] * a.g.N1 * a.g.N2 + (long long)bk.y * a.g.N2 + i2;
     stride = a.g.N1 * a.g.N2;
   }
+  if (valid) valid = grid_range_ok(a.g, base, base + (long long)(N - 1) * stride, BC_STRIDED);
+  if (!__any_sync(0xffffffffu, valid)) return;  // the same 32 pencils in every warp
   float2* K = a.K;
   auto gld = [&](int e) { return valid ? K[base + e * stride] : make_float2(0.f, 0.f); };
   auto gst = [&](int e, float2 v) {
@@ -568,6 +570,8 @@ __device__ __forceinline__ MidPencil mid_pencil(const PassArgs& a, const Blk& bk
   if (m.valid && a.active) m.valid = sub_active(a.active, a.g, j, a.tb.sub[1][i1], a.tb.sub[2][i2c]);
   m.base = (long long)off0 * a.g.N1 * a.g.N2 + i1 * a.g.N2 + i2;
   m.stride = a.g.N1 * a.g.N2;
+  if (m.valid)
+    m.valid = grid_range_ok(a.g, m.base, m.base + (long long)(a.g.ax[0].n[j] - 1) * m.stride, BC_MID);
   m.pl = a.tb.p2[1][i1] + a.tb.p2[2][i2c];
   m.sc = a.tb.invn[0][off0] * a.tb.invn[1][i1] * a.tb.invn[2][i2c];
   m.p20 = a.tb.p2[0] + off0;

@@ -184,7 +184,6 @@ __global__ void __launch_bounds__(32 * warps_for(N), tma_min_blocks(N)) k_stride
     if (valid && a.active)
       valid = AXIS == 1 ? sub_active(a.active, a.g, a.tb.sub[0][tl.y], j, a.tb.sub[2][i2])
                         : sub_active(a.active, a.g, j, a.tb.sub[1][tl.y], a.tb.sub[2][i2]);
-    if (!__any_sync(0xffffffffu, valid)) return;  // no pencil of this tile is active: nothing to store
     long long base, stride;
     if (AXIS == 1) {
       base = (long long)tl.y * a.g.N1 * a.g.N2 + (long long)a.g.ax[1].off[j] * a.g.N2 + i2;
@@ -193,6 +192,8 @@ __global__ void __launch_bounds__(32 * warps_for(N), tma_min_blocks(N)) k_stride
       base = (long long)a.g.ax[0].off[j] * a.g.N1 * a.g.N2 + (long long)tl.y * a.g.N2 + i2;
       stride = a.g.N1 * a.g.N2;
     }
+    if (valid) valid = grid_range_ok(a.g, base, base + (long long)(N - 1) * stride, BC_TMA);
+    if (!__any_sync(0xffffffffu, valid)) return;  // no pencil of this tile is active: nothing to store
     auto sld = [&](int e) { return sm[e][lane]; };
     auto gst = [&](int e, float2 v) {
       if (valid) K[base + e * stride] = v;
@@ -227,9 +228,10 @@ __global__ void __launch_bounds__(32 * warps_for(N), tma_min_blocks(N)) k_mid_tm
     bool valid = i2 < a.g.N2;
     const long long i2c = valid ? i2 : 0;
     if (valid && a.active) valid = sub_active(a.active, a.g, j, a.tb.sub[1][i1], a.tb.sub[2][i2c]);
-    if (!__any_sync(0xffffffffu, valid)) return;  // no pencil of this tile is active: nothing to store
     const long long base = (long long)off0 * a.g.N1 * a.g.N2 + i1 * a.g.N2 + i2;
     const long long stride = a.g.N1 * a.g.N2;
+    if (valid) valid = grid_range_ok(a.g, base, base + (long long)(N - 1) * stride, BC_TMA);
+    if (!__any_sync(0xffffffffu, valid)) return;  // no pencil of this tile is active: nothing to store
     const float pl = a.tb.p2[1][i1] + a.tb.p2[2][i2c];
     const float sc = a.tb.invn[0][off0] * a.tb.invn[1][i1] * a.tb.invn[2][i2c];
     const float* p20 = a.tb.p2[0] + off0;
