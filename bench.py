@@ -533,6 +533,20 @@ def run_batch(args, pkg, torch, ws, rank, dev):
     clk = clocks.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
     value = whole_job_rate(vox * K, ws, ms / 1e3)
+    # the other form of the batch (fused <-> graph of every plan's own launches)
+    other = None
+    b.set_fused(not fused)
+    b.iterate(max(args.warmup, 3), 0.0, no_poll=True)
+    n_launch2, fused2 = b.launches_per_iteration()
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    b.iterate(K, 0.0, no_poll=True)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms2 = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
+    other = {"value": whole_job_rate(vox * K, ws, ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2 / K, "fused": fused2,
+             "launches_per_iteration": n_launch2}
+    b.set_fused(fused)
     # the same solves one after another, each with its own graph replays
     t0 = time.perf_counter()
     for p in plans:
@@ -577,6 +591,7 @@ def run_batch(args, pkg, torch, ws, rank, dev):
                 "batch": {"fused": fused, "launches_per_iteration": n_launch,
                           "how": "one launch per pass and subdomain edge over all solves" if fused else
                                  "one graph of every solve's own launches on forked streams"},
+                "other_form": other,
                 "sequential": {"value": vox * K / seq, "unit": UNIT,
                                "how": "the same 64 solves one after another, each with its own graph replays"},
                 "time_to_tol": ttt}

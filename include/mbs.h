@@ -350,6 +350,13 @@ MBS_API mbs_status mbs_batch_iterate(mbs_batch *batch, int32_t n_iter, double to
  * holds every plan's own launches.
  */
 MBS_API int32_t mbs_batch_launches_per_iteration(mbs_batch *batch, int32_t *fused);
+/*
+ * Choose the batch's form: on = 1 the fused form (MBS_EINVAL if the plans do
+ * not allow it), 0 the graph of every plan's own launches. mbs_batch_create
+ * picks the fused form whenever the plans allow it. Iterates are the same in
+ * both forms.
+ */
+MBS_API mbs_status mbs_batch_set_fused(mbs_batch *batch, int32_t on);
 MBS_API void mbs_batch_destroy(mbs_batch *batch);
 
 MBS_API void mbs_plan_destroy(mbs_plan *plan);

@@ -93,6 +93,8 @@ def load_library(path=None):
     lib.mbs_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), vp, i32]
     lib.mbs_batch_iterate.argtypes = [vp, i32, dbl, i32, C.POINTER(i32), C.POINTER(dbl), C.POINTER(i32)]
     lib.mbs_batch_launches_per_iteration.argtypes = [vp, C.POINTER(i32)]
+    lib.mbs_batch_set_fused.argtypes = [vp, i32]
+    lib.mbs_batch_set_fused.restype = C.c_int
     lib.mbs_batch_launches_per_iteration.restype = C.c_int32
     lib.mbs_batch_destroy.argtypes = [vp]
     lib.mbs_batch_destroy.restype = None
@@ -342,7 +344,7 @@ class Plan:
 class Batch:
     """Several plans advanced together (``mbs_batch_*`` in include/mbs.h)."""
 
-    def __init__(self, plans, stream=None, graph_iters=0):
+    def __init__(self, plans, stream=None, graph_iters=0, fused=None):
         self.lib = load_library()
         self.plans = list(plans)
         arr = (C.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
@@ -351,6 +353,8 @@ class Batch:
                                                    C.c_void_p(int(stream)) if stream is not None else None,
                                                    int(graph_iters)))
         self.handle = h
+        if fused is not None:
+            _check(self.lib, self.lib.mbs_batch_set_fused(self.handle, 1 if fused else 0))
 
     def iterate(self, n_iter, tol=0.0, no_poll=False):
         """Returns a list of (status_name, iterations, residual), one per plan."""
@@ -361,6 +365,10 @@ class Batch:
         _check(self.lib, self.lib.mbs_batch_iterate(self.handle, int(n_iter), float(tol), 1 if no_poll else 0,
                                                     it, res, sts), ok=(0, 4))
         return [(STATUS[sts[i]], it[i], res[i]) for i in range(n)]
+
+    def set_fused(self, on):
+        """Run as one launch per pass and edge over all plans (on) or as a graph of every plan's own launches."""
+        _check(self.lib, self.lib.mbs_batch_set_fused(self.handle, 1 if on else 0))
 
     def launches_per_iteration(self):
         """(kernel launches per iteration of the whole batch, fused form or not)."""

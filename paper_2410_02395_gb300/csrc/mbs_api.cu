@@ -302,7 +302,11 @@ size_t layout(mbs_plan* p, char* base, bool assign) {
       if (!fft_size_compiled(gz.n)) p->bl_axis2 = true;
     p->partials = (double*)ppart;
     p->n_rows_partials = nrows_partials;
-    p->n_shell_partials = kShellBlocks;
+    // the layer update's grid: about 64 grid rows per block, between one block
+    // per SM and kShellBlocks (each block pays a fixed cost for its FP64
+    // partial and ticket, which dominated small grids at kShellBlocks)
+    const long long srows = p->N[0] * p->N[1];
+    p->n_shell_partials = (int)std::max(152ll, std::min((long long)kShellBlocks, (srows + 63) / 64));
     p->state = (DevState*)pst;
     p->free_state = (DevState*)pfst;
     p->history = (double*)phist;
@@ -995,7 +999,7 @@ cudaError_t run_rows_last(mbs_plan* p, PassArgs a, int mode, bool partials, Reco
     set_len_tables(p, a, gz.n);
     a.partials = partials ? p->partials : nullptr;
     a.slot0 = poff;
-    a.n_total = p->n_rows_partials + (p->has_shell ? kShellBlocks : 0);
+    a.n_total = p->n_rows_partials + (p->has_shell ? p->n_shell_partials : 0);
     a.fin = (fin && gi + 1 == p->groups[2].size()) ? p->state : nullptr;
     a.hist = p->history;
     poff += nrb * gz.nsub;
@@ -1037,11 +1041,11 @@ cudaError_t enqueue_iteration_res(mbs_plan* p, Recorder* rec) {
     s.mode = SHELL_UPDATE_RES;
     s.partials = p->partials;  // zeros: |r'_n|^2 was summed by the last pass
     s.slot0 = p->n_rows_partials;
-    s.n_total = p->n_rows_partials + kShellBlocks;
+    s.n_total = p->n_rows_partials + p->n_shell_partials;
     s.fin = p->state;
     s.hist = p->history;
     if (rec) rec->begin(KK_SHELL_UPDATE);
-    e = fused ? launch_shell_rows(s, kShellBlocks, p->stream) : launch_shell(s, kShellBlocks, p->stream);
+    e = fused ? launch_shell_rows(s, p->n_shell_partials, p->stream) : launch_shell(s, p->n_shell_partials, p->stream);
     if (rec) rec->end();
     if (e) return e;
   }
@@ -1079,11 +1083,11 @@ cudaError_t enqueue_iteration(mbs_plan* p, Recorder* rec) {
     s.mode = SHELL_UPDATE_ITER;
     s.partials = p->partials;
     s.slot0 = p->n_rows_partials;
-    s.n_total = p->n_rows_partials + kShellBlocks;
+    s.n_total = p->n_rows_partials + p->n_shell_partials;
     s.fin = p->state;
     s.hist = p->history;
     if (rec) rec->begin(KK_SHELL_UPDATE);
-    e = fused ? launch_shell_rows(s, kShellBlocks, p->stream) : launch_shell(s, kShellBlocks, p->stream);
+    e = fused ? launch_shell_rows(s, p->n_shell_partials, p->stream) : launch_shell(s, p->n_shell_partials, p->stream);
     if (rec) rec->end();
     if (e) return e;
   }
@@ -1970,7 +1974,7 @@ struct BatchLaunch {
   dim3 grid;
   size_t smem;
   size_t off;      // byte offset of the argument array
-  long long maxthr;  // kind 4: largest thread count
+  long long maxthr;  // kind 4: largest thread count; kind 5: largest block count
   int max_slots;   // kind 5: largest 2 t S_2
 };
 
@@ -2093,7 +2097,7 @@ mbs_status batch_build(mbs_batch* b) {
           if (kind == 1) {
             a.partials = p->partials;
             a.slot0 = poff;
-            a.n_total = p->n_rows_partials + kShellBlocks;
+            a.n_total = p->n_rows_partials + p->n_shell_partials;
             a.fin = nullptr;  // the layer update ends the iteration
             a.hist = p->history;
             poff += nrb * gz.nsub;
@@ -2133,22 +2137,26 @@ mbs_status batch_build(mbs_batch* b) {
   {  // the layer update (kind 5) ends every plan's iteration
     std::vector<ShellArgs> v;
     int max_slots = 0;
+    long long max_blocks = 0;
     for (mbs_plan* p : b->plans) {
       ShellArgs sa = shell_args(p);
       sa.state = p->state;
       sa.mode = SHELL_UPDATE_ITER;
       sa.partials = p->partials;
       sa.slot0 = p->n_rows_partials;
-      sa.n_total = p->n_rows_partials + kShellBlocks;
+      sa.n_total = p->n_rows_partials + p->n_shell_partials;
+      sa.nblocks = p->n_shell_partials;
       sa.fin = p->state;
       sa.hist = p->history;
       v.push_back(sa);
       max_slots = std::max(max_slots, p->a[2] > 0 ? 2 * t * p->S[2] : 0);
+      max_blocks = std::max(max_blocks, (long long)p->n_shell_partials);
     }
     BatchLaunch L = {};
     L.kind = 5;
     L.m = (int)v.size();
     L.max_slots = max_slots;
+    L.maxthr = max_blocks;  // the largest plan's block count
     L.off = push(v.data(), v.size() * sizeof(ShellArgs));
     b->launches.push_back(L);
   }
@@ -2170,7 +2178,7 @@ cudaError_t batch_launch_one(mbs_batch* b, const BatchLaunch& L, cudaStream_t st
     return launch_pass_batch(L.n, L.kind, L.inv, b->t == 8 ? 8 : 0, (const PassArgs*)(base + L.off), L.grid, L.smem,
                              st);
   if (L.kind == 4) return launch_corr_side_batch((const CorrArgs*)(base + L.off), L.m, b->t, L.maxthr, st);
-  return launch_shell_rows_batch((const ShellArgs*)(base + L.off), L.m, b->t, L.max_slots, kShellBlocks, st);
+  return launch_shell_rows_batch((const ShellArgs*)(base + L.off), L.m, b->t, L.max_slots, L.maxthr, st);
 }
 
 // One iteration of every plan in the fused form. Consecutive launches of the
@@ -2361,6 +2369,35 @@ mbs_status mbs_batch_iterate(mbs_batch* b, int32_t n_iter, double tol, int32_t n
   }
   if (worst == MBS_ENOCONV) g_err = "some solves did not reach tol";
   return worst;
+}
+
+mbs_status mbs_batch_set_fused(mbs_batch* b, int32_t on) {
+  g_err.clear();
+  if (!b) return fail(MBS_EINVAL, "null batch");
+  if (on && !batch_fusable(b)) return fail(MBS_EINVAL, "the plans of this batch do not allow the fused form");
+  if ((on != 0) == b->fused) return MBS_OK;
+  if (on && b->side.empty()) {  // side streams for the per-edge launches of one pass
+    bool ok = b->stage || cudaEventCreateWithFlags(&b->stage, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < 16 && ok; k++) {
+      cudaStream_t sk;
+      cudaEvent_t ek;
+      ok = cudaStreamCreateWithFlags(&sk, cudaStreamNonBlocking) == cudaSuccess;
+      if (ok) b->side.push_back(sk);
+      ok = ok && cudaEventCreateWithFlags(&ek, cudaEventDisableTiming) == cudaSuccess;
+      if (ok) b->side_done.push_back(ek);
+    }
+    if (!ok) return fail(MBS_ECUDA, "side stream creation failed");
+  }
+  CU(cudaStreamSynchronize(b->stream));
+  for (int w = 0; w < 2; w++)
+    if (b->ready[w]) {
+      cudaGraphExecDestroy(b->graph[w]);
+      b->ready[w] = false;
+    }
+  b->fused = on != 0;
+  b->launches.clear();
+  for (size_t i = 0; i < b->plans.size(); i++) b->gen[i] = ~0u;  // arguments built again at the next iterate
+  return MBS_OK;
 }
 
 int32_t mbs_batch_launches_per_iteration(mbs_batch* b, int32_t* fused) {

@@ -886,8 +886,10 @@ __global__ void __launch_bounds__(256, J == 1 ? 4 : 3) k_shell_rows(const __grid
 template <int MODE, int TC, int J>
 __global__ void __launch_bounds__(256, J == 1 ? 4 : 3) k_shell_rows_batch(const ShellArgs* __restrict__ d) {
   __shared__ ShellArgs a;
+  const unsigned nb = (unsigned)d[blockIdx.y].nblocks;
+  if (blockIdx.x >= nb) return;
   stage_args(&a, &d[blockIdx.y]);
-  shell_rows_body<MODE, TC, J>(a, blockIdx.x, gridDim.x);
+  shell_rows_body<MODE, TC, J>(a, blockIdx.x, nb);
 }
 
 bool shell_rows_supported(const GridDesc& g) {

@@ -149,6 +149,7 @@ struct ShellArgs {
   int mode;
   const float2* cW;     // c W (t x t), for the fused axis-2 corrections of launch_shell_rows
   const int* active;    // subdomain activation: null (all active) or one flag per subdomain
+  int nblocks;          // batched layer update: this plan's block count (its grid is the largest plan's)
 };
 
 // One step of the plain form of the iteration (MBS_FLAG_PLAIN_STEPS): every

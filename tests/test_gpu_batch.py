@@ -30,13 +30,17 @@ def problems():
     return frequency_batch(count=4, seed=7, box=7.0, spheres=5, r_range=(0.5, 1.5), t=4)
 
 
+@pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("n_iter", [7, 25])
-def test_batch_equals_individual_plans(problems, n_iter):
+def test_batch_equals_individual_plans(problems, n_iter, fused):
+    """Both forms of the batch: one launch per pass and edge over all plans, and a
+    graph of every plan's own launches."""
     import paper_2410_02395_gb300 as pkg
 
     assert len({p["shape"] for p, _, _ in problems}) > 1  # uneven grids in one batch
     batched = _plans(problems)
-    b = pkg.Batch(batched, graph_iters=10)
+    b = pkg.Batch(batched, graph_iters=10, fused=fused)
+    assert b.launches_per_iteration()[1] == fused
     res = b.iterate(n_iter, 0.0, no_poll=True)
     assert [r[1] for r in res] == [n_iter] * len(problems)
     single = _plans(problems)
