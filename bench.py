@@ -589,7 +589,8 @@ def run_batch(args, pkg, torch, ws, rank, dev):
                 "clocks": clk,
                 "gpu_launches": n_launch * K,
                 "batch": {"fused": fused, "launches_per_iteration": n_launch,
-                          "how": "one launch per pass and subdomain edge over all solves" if fused else
+                          "how": "one launch per pass and subdomain edge over the solves of each cluster "
+                                 "(solves sharing an edge), clusters side by side" if fused else
                                  "one graph of every solve's own launches on forked streams"},
                 "other_form": other,
                 "sequential": {"value": vox * K / seq, "unit": UNIT,

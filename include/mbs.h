@@ -342,12 +342,14 @@ MBS_API mbs_status mbs_batch_iterate(mbs_batch *batch, int32_t n_iter, double to
                                      double *residuals, int32_t *statuses);
 /*
  * Kernel launches per iteration of the whole batch (-1 on error); *fused
- * (nullable) is 1 when the batch runs in its fused form: one launch per pass
- * and subdomain edge over all plans (grid.z selecting the plan), which applies
- * when every plan iterates in the default x form with FP32 corrections, every
- * subdomain edge is a mixed-radix length of at most 128 (and at least 2t on
- * corrected axes 0 and 1) and all plans share t; otherwise the batch graph
- * holds every plan's own launches.
+ * (nullable) is 1 when the batch runs in its fused form: plans that share a
+ * subdomain edge along some axis form a cluster, and each cluster takes one
+ * launch per pass and subdomain edge over its plans (grid.z or grid.y selecting
+ * the plan); the clusters run side by side on streams of the batch. The form
+ * applies when every plan iterates in the default x form with FP32
+ * corrections, every subdomain edge is a mixed-radix length of at most 128
+ * (and at least 2t on corrected axes 0 and 1) and all plans share t; otherwise
+ * the batch graph holds every plan's own launches.
  */
 MBS_API int32_t mbs_batch_launches_per_iteration(mbs_batch *batch, int32_t *fused);
 /*

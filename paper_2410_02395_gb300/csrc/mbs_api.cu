@@ -1965,8 +1965,10 @@ mbs_status mbs_profile_iterations(mbs_plan* p, int32_t n_iter, int32_t launches[
 // leaves its kernels at once (its own stop flag).
 // ---------------------------------------------------------------------------
 // One launch of the fused batch: a pass (or correction, layer update) of every
-// plan that has it, for one edge; its argument array sits at `off` in desc_mem.
+// plan of one cluster that has it, for one edge; its argument array sits at
+// `off` in desc_mem.
 struct BatchLaunch {
+  int cluster;     // plans that share a subdomain edge on some axis (batch_build)
   int kind;        // 0 first pass, 1 last pass, 2 axis-1 pass, 3 axis-0 pass, 4 corrections, 5 layer update
   int n;           // edge (kinds 0-3), axis (kind 4)
   bool inv;        // axis-1 pass: inverse
@@ -1995,10 +1997,10 @@ struct mbs_batch {
   void* desc_mem;
   size_t desc_cap;
   std::vector<BatchLaunch> launches;
-  // the launches of one pass (one per edge) run side by side on these streams
+  int nclusters;
+  // each cluster's launches run in order on one of these streams, the clusters side by side
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> side_done;
-  cudaEvent_t stage;
 };
 
 namespace {
@@ -2029,6 +2031,40 @@ bool batch_fusable(const mbs_batch* b) {
 // copied to the device (again after any mbs_set_source: they hold the source box).
 mbs_status batch_build(mbs_batch* b) {
   b->launches.clear();
+  // Clusters: plans that share a subdomain edge along some axis are joined, so
+  // that every launch (one per pass and edge) holds plans of one cluster only.
+  // The clusters' launch sequences are independent and run side by side; a
+  // cluster's passes follow one another on its own stream.
+  const int np = (int)b->plans.size();
+  std::vector<int> parent(np);
+  for (int i = 0; i < np; i++) parent[i] = i;
+  auto find = [&](int i) {
+    while (parent[i] != i) i = parent[i] = parent[parent[i]];
+    return i;
+  };
+  std::map<std::pair<int, int>, int> first_with;  // (axis, edge) -> a plan that has it
+  for (int i = 0; i < np; i++)
+    for (int d = 0; d < 3; d++)
+      for (int s = 0; s < b->plans[i]->S[d]; s++) {
+        const auto key = std::make_pair(d, b->plans[i]->sizes[d][s]);
+        auto it = first_with.find(key);
+        if (it == first_with.end())
+          first_with[key] = i;
+        else
+          parent[find(i)] = find(it->second);
+      }
+  std::map<int, int> cluster_of_root;
+  std::vector<std::vector<mbs_plan*>> clusters;
+  for (int i = 0; i < np; i++) {
+    const int r = find(i);
+    auto it = cluster_of_root.find(r);
+    if (it == cluster_of_root.end()) {
+      it = cluster_of_root.emplace(r, (int)clusters.size()).first;
+      clusters.emplace_back();
+    }
+    clusters[it->second].push_back(b->plans[i]);
+  }
+  b->nclusters = (int)clusters.size();
   std::vector<char> host;
   auto push = [&](const void* src, size_t bytes) {
     const size_t off = (host.size() + 255) & ~size_t(255);
@@ -2037,12 +2073,14 @@ mbs_status batch_build(mbs_batch* b) {
     return off;
   };
   const int t = b->t;
+  int cl = 0;                           // the cluster being built
+  const std::vector<mbs_plan*>* ps = nullptr;  // its plans
   // corrections of x (kind 4) on axes 0 and 1, then the passes, then the corrections of e
   auto corr_launches = [&](bool on_e) {
     for (int d = 0; d < 2; d++) {
       std::vector<CorrArgs> v;
       long long maxthr = 0;
-      for (mbs_plan* p : b->plans) {
+      for (mbs_plan* p : *ps) {
         if (p->a[d] <= 0) continue;
         CorrArgs c;
         memset(&c, 0, sizeof(c));
@@ -2061,6 +2099,7 @@ mbs_status batch_build(mbs_batch* b) {
       }
       if (v.empty()) continue;
       BatchLaunch L = {};
+      L.cluster = cl;
       L.kind = 4;
       L.n = d;
       L.m = (int)v.size();
@@ -2069,12 +2108,11 @@ mbs_status batch_build(mbs_batch* b) {
       b->launches.push_back(L);
     }
   };
-  corr_launches(false);
   // pass kind k over the size groups of axis ax, for every edge n present in any plan
   auto pass_launches = [&](int kind, int ax, bool inv) {
     std::map<int, std::vector<PassArgs>> by_n;
     std::map<int, std::pair<unsigned, unsigned>> ext;  // largest grid x, y per edge
-    for (mbs_plan* p : b->plans) {
+    for (mbs_plan* p : *ps) {
       int poff = 0;
       const int nrb = nrow_blocks(p);
       for (size_t gi = 0; gi < p->groups[ax].size(); gi++) {
@@ -2118,6 +2156,7 @@ mbs_status batch_build(mbs_batch* b) {
     for (auto& kv : by_n) {
       const int n = kv.first;
       BatchLaunch L = {};
+      L.cluster = cl;
       L.kind = kind;
       L.n = n;
       L.inv = inv;
@@ -2128,17 +2167,12 @@ mbs_status batch_build(mbs_batch* b) {
       b->launches.push_back(L);
     }
   };
-  pass_launches(0, 2, false);
-  pass_launches(2, 1, false);
-  pass_launches(3, 0, false);
-  pass_launches(2, 1, true);
-  pass_launches(1, 2, false);
-  corr_launches(true);
-  {  // the layer update (kind 5) ends every plan's iteration
+  // the layer update (kind 5) ends every plan's iteration
+  auto shell_launch = [&]() {
     std::vector<ShellArgs> v;
     int max_slots = 0;
     long long max_blocks = 0;
-    for (mbs_plan* p : b->plans) {
+    for (mbs_plan* p : *ps) {
       ShellArgs sa = shell_args(p);
       sa.state = p->state;
       sa.mode = SHELL_UPDATE_ITER;
@@ -2153,12 +2187,24 @@ mbs_status batch_build(mbs_batch* b) {
       max_blocks = std::max(max_blocks, (long long)p->n_shell_partials);
     }
     BatchLaunch L = {};
+    L.cluster = cl;
     L.kind = 5;
     L.m = (int)v.size();
     L.max_slots = max_slots;
     L.maxthr = max_blocks;  // the largest plan's block count
     L.off = push(v.data(), v.size() * sizeof(ShellArgs));
     b->launches.push_back(L);
+  };
+  for (cl = 0; cl < b->nclusters; cl++) {
+    ps = &clusters[cl];
+    corr_launches(false);
+    pass_launches(0, 2, false);
+    pass_launches(2, 1, false);
+    pass_launches(3, 0, false);
+    pass_launches(2, 1, true);
+    pass_launches(1, 2, false);
+    corr_launches(true);
+    shell_launch();
   }
   if (host.size() > b->desc_cap) {  // (re)allocate the argument arrays
     if (b->desc_mem) cudaFree(b->desc_mem);
@@ -2181,37 +2227,32 @@ cudaError_t batch_launch_one(mbs_batch* b, const BatchLaunch& L, cudaStream_t st
   return launch_shell_rows_batch((const ShellArgs*)(base + L.off), L.m, b->t, L.max_slots, L.maxthr, st);
 }
 
-// One iteration of every plan in the fused form. Consecutive launches of the
-// same pass (one per edge: disjoint subdomains, so independent) run side by side
-// on the batch's side streams; the passes follow one another. The correction
-// launches stay in order (axis 1 adds to what axis 0 wrote).
-cudaError_t batch_enqueue_fused(mbs_batch* b) {
-  const size_t nl = b->launches.size();
-  size_t i = 0;
-  while (i < nl) {
-    const BatchLaunch& L0 = b->launches[i];
-    size_t j = i + 1;
-    if (L0.kind <= 3)
-      while (j < nl && b->launches[j].kind == L0.kind && b->launches[j].inv == L0.inv) j++;
-    cudaError_t e;
-    if (j - i == 1 || b->side.empty()) {
-      for (size_t k = i; k < j; k++)
-        if ((e = batch_launch_one(b, b->launches[k], b->stream))) return e;
-    } else {
-      if ((e = cudaEventRecord(b->stage, b->stream))) return e;
-      const size_t ns = std::min(j - i, b->side.size());
-      for (size_t k = 0; k < ns; k++)
-        if ((e = cudaStreamWaitEvent(b->side[k], b->stage, 0))) return e;
-      for (size_t k = i; k < j; k++)
-        if ((e = batch_launch_one(b, b->launches[k], b->side[(k - i) % ns]))) return e;
-      for (size_t k = 0; k < ns; k++) {
-        if ((e = cudaEventRecord(b->side_done[k], b->side[k]))) return e;
-        if ((e = cudaStreamWaitEvent(b->stream, b->side_done[k], 0))) return e;
+// `iters` iterations of every plan in the fused form: cluster c's launches, in
+// order, on side stream c mod 16 (a stream may carry several clusters one after
+// another), forked from and joined to the batch's stream.
+cudaError_t batch_enqueue_fused(mbs_batch* b, int iters) {
+  const int ns = (int)std::min(b->side.size(), b->side_done.size());
+  std::vector<char> used(ns, 0);
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < b->nclusters && !e; c++) {
+    cudaStream_t sc = b->stream;
+    if (ns > 1 && b->nclusters > 1) {
+      sc = b->side[c % ns];
+      if (!used[c % ns]) {
+        e = cudaStreamWaitEvent(sc, b->fork, 0);
+        used[c % ns] = 1;
       }
     }
-    i = j;
+    for (int k = 0; k < iters && !e; k++)
+      for (const BatchLaunch& L : b->launches)
+        if (L.cluster == c && !e) e = batch_launch_one(b, L, sc);
   }
-  return cudaSuccess;
+  for (int k = 0; k < ns && !e; k++)
+    if (used[k]) {
+      e = cudaEventRecord(b->side_done[k], b->side[k]);
+      if (!e) e = cudaStreamWaitEvent(b->stream, b->side_done[k], 0);
+    }
+  return e;
 }
 
 mbs_status batch_capture(mbs_batch* b, int which, int iters) {
@@ -2222,9 +2263,7 @@ mbs_status batch_capture(mbs_batch* b, int which, int iters) {
   cudaGraph_t g;
   CU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaEventRecord(b->fork, b->stream);
-  if (b->fused) {
-    for (int k = 0; k < iters && !e; k++) e = batch_enqueue_fused(b);
-  }
+  if (b->fused && !e) e = batch_enqueue_fused(b, iters);
   for (size_t i = 0; i < b->plans.size() && !e && !b->fused; i++) {
     mbs_plan* p = b->plans[i];
     e = cudaStreamWaitEvent(p->stream, b->fork, 0);
@@ -2275,7 +2314,7 @@ mbs_status mbs_batch_create(mbs_batch** out, int32_t nplans, mbs_plan* const* pl
   b->desc_cap = 0;
   b->t = plans[0]->t;
   b->fused = batch_fusable(b);
-  b->stage = nullptr;
+  b->nclusters = 0;
   if (stream) {
     b->stream = (cudaStream_t)stream;
   } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -2285,8 +2324,7 @@ mbs_status mbs_batch_create(mbs_batch** out, int32_t nplans, mbs_plan* const* pl
   b->join.assign(nplans, nullptr);
   bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
             cudaMallocHost((void**)&b->host_states, nplans * sizeof(DevState)) == cudaSuccess;
-  if (ok && b->fused) {  // side streams for the per-edge launches of one pass
-    ok = cudaEventCreateWithFlags(&b->stage, cudaEventDisableTiming) == cudaSuccess;
+  if (ok && b->fused) {  // side streams for the clusters of the fused form
     for (int k = 0; k < 16 && ok; k++) {
       cudaStream_t sk;
       cudaEvent_t ek;
@@ -2376,8 +2414,8 @@ mbs_status mbs_batch_set_fused(mbs_batch* b, int32_t on) {
   if (!b) return fail(MBS_EINVAL, "null batch");
   if (on && !batch_fusable(b)) return fail(MBS_EINVAL, "the plans of this batch do not allow the fused form");
   if ((on != 0) == b->fused) return MBS_OK;
-  if (on && b->side.empty()) {  // side streams for the per-edge launches of one pass
-    bool ok = b->stage || cudaEventCreateWithFlags(&b->stage, cudaEventDisableTiming) == cudaSuccess;
+  if (on && b->side.empty()) {  // side streams for the clusters of the fused form
+    bool ok = true;
     for (int k = 0; k < 16 && ok; k++) {
       cudaStream_t sk;
       cudaEvent_t ek;
@@ -2432,7 +2470,6 @@ void mbs_batch_destroy(mbs_batch* b) {
   if (b->desc_mem) cudaFree(b->desc_mem);
   for (cudaStream_t sk : b->side) cudaStreamDestroy(sk);
   for (cudaEvent_t ek : b->side_done) cudaEventDestroy(ek);
-  if (b->stage) cudaEventDestroy(b->stage);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
