@@ -203,9 +203,12 @@ __host__ __device__ constexpr RadixPlan make_plan(int n) {
 
 __host__ __device__ constexpr bool fft_size_supported(int n) { return n >= 1 && make_plan(n).nr >= 0; }
 
-// Warps per CTA for a length-N tile: about 16 elements per thread.
+// Warps per CTA for a length-N tile: about 16 elements per thread, and four
+// warps from N = 33 to 63, where two or three warps left the first pass
+// limited to a third of the SM's warp slots by its shared memory (the tile and
+// the staged neighbour layers of the fused corrections take about 20 KB).
 __host__ __device__ constexpr int warps_for(int n) {
-  return n <= 32 ? 2 : (n / 16 > 32 ? 32 : n / 16);
+  return n <= 32 ? 2 : (n < 64 ? 4 : (n / 16 > 32 ? 32 : n / 16));
 }
 
 constexpr int kPad = 33;  // shared tile row pitch in float2
