@@ -74,7 +74,7 @@ typedef enum mbs_operator {
   MBS_OP_IFFT = 7       /* inverse DFT (1/n0 n1 n2) of every subdomain                           */
 } mbs_operator;
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define MBS_MAX_SPLIT 16 /* subdomains per axis */
 #define MBS_MAX_T 40     /* truncation width (Fig. 7 sweeps t = 0..40): every t in 1..40; widths
                             1..16, 20, 24 and 32 have specialised correction kernels, the others a

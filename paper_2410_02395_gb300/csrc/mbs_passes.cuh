@@ -668,7 +668,7 @@ constexpr int mid_min_blocks(int n) { return fft_min_blocks(n); }
 
 // Per kernel (keyed by its address): above 48 KB, the dynamic shared-memory
 // opt-in for the largest size requested so far. The L1/shared split is left to
-// the driver: these kernels read twiddles, tables and B through L1.
+// the CUDA driver: these kernels read twiddles, tables and B through L1.
 struct KernelAttrs {
   std::mutex mu;
   std::unordered_map<const void*, size_t> smem;     // opted-in dynamic bytes
