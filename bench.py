@@ -616,6 +616,7 @@ def main():
     ap.add_argument("--ttt", action="store_true", help="run the time-to-tolerance leg (long at 1280^3)")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance leg of C4")
     ap.add_argument("--ttt-max-iter", type=int, default=40000)
+    ap.add_argument("--ttt-chunk", type=int, default=0, help="print the --ttt leg's progress every N iterations")
     ap.add_argument("--ttt-history", default="", help="file (.npy) for the residual history of the --ttt leg")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_TEXT),
                     help="benchmark workload (default: the 1280^3 configuration C5)")
@@ -752,7 +753,17 @@ def main():
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             pr.set_source(src_dev)
-            st_tol, it_tol, eps_tol = pr.iterate(args.ttt_max_iter, params["tol"])
+            if args.ttt_chunk > 0:  # progress on stderr every ttt_chunk iterations (same solve)
+                it_tol = 0
+                while it_tol < args.ttt_max_iter:
+                    st_tol, it_tol, eps_tol = pr.iterate(min(args.ttt_chunk, args.ttt_max_iter - it_tol),
+                                                         params["tol"])
+                    print(json.dumps({"iterations": it_tol, "residual": eps_tol, "status": st_tol,
+                                      "seconds": time.perf_counter() - t0}), file=sys.stderr, flush=True)
+                    if st_tol != "MBS_ENOCONV":
+                        break
+            else:
+                st_tol, it_tol, eps_tol = pr.iterate(args.ttt_max_iter, params["tol"])
             torch.cuda.synchronize(dev)
             secs = time.perf_counter() - t0
             ttt_line = {"tol": params["tol"], "status": st_tol, "iterations": it_tol, "residual": eps_tol,
