@@ -52,10 +52,13 @@ WORKLOAD_TEXT = {
           "Gaussian-beam plane source",
     "C4": "C4: 64 independent frequency solves, lambda uniform in [0.8,1.2] on one 24-unit box at lambda/4 "
           "(grids 80^3-120^3), each split 2x2x2 into 7-smooth halves, t=8, same spheres, point sources; "
-          "one CUDA graph over all solves",
+          "advanced together as one batch",
     "C5": "C5: 1280^3 grid at lambda/4, 4x4x4 subdomains of 320^3, t=8, spheres to 30% fill, point source",
     "C2P": "C2P: the C2 recipe on a 246^3 grid, 2x2x2 subdomains of 123^3 (123 = 3 x 41: Bluestein transforms "
            "on every axis), t=8",
+    "P43": "P43: the geometry of the paper's large example, 1320x1280x1280 at lambda/4, 20-px absorbing layers on "
+           "the x faces only, y and z periodic, packed spheres r = 24 px with 24-px clearance (n = 1.33 + 0.01i), "
+           "plane source at x = 20; 5x4x4 subdomains (x: 280, 280, 256, 252, 252; y, z: 320 with periodic seams), t=8",
 }
 METRIC = "voxel-iterations/s on 1 GB300 (mixed vs plain FP32, ≤1e-4 vs FP64); time-to-tol"
 UNIT = "voxel-iterations/s"
@@ -205,7 +208,7 @@ def build_problem(name):
 # Bounded samples of a workload's recipe for the oracle on the host: the recipe
 # on a sub-box with one subdomain of the workload's subdomain edge (wrap-removal
 # corrections on every axis), so that the per-voxel work matches.
-CPU_SAMPLE = {"C5": (320, 320, 320), "C3": (128, 128, 128), "C2": (128, 128, 128), "C2P": (123, 123, 123),
+CPU_SAMPLE = {"C5": (320, 320, 320), "P43": (320, 320, 320), "C3": (128, 128, 128), "C2": (128, 128, 128), "C2P": (123, 123, 123),
               "C1": (64, 64, 64)}
 REFERENCE_SAMPLE = (128, 128, 128)  # per step of the reference arm (a few seconds each)
 
@@ -662,6 +665,8 @@ def main():
     src_dev = torch.from_numpy(src).to(dev)
     kw = dict(boundary_widths=params["widths"], split=params["split"], truncation=params["t"],
               periodic=params["periodic"], stream=stream.cuda_stream)
+    if params.get("split_sizes"):
+        kw["split_sizes"] = params["split_sizes"]
     with torch.cuda.stream(stream):
         plan = pkg.Plan(shape, params["pixel"], params["wavelength"], n_dev, **kw)
         info = plan.info()

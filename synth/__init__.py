@@ -10,6 +10,8 @@ from .media import (  # noqa: F401
     gaussian_random_field_medium,
     point_source,
     gaussian_beam_plane_source,
+    packed_spheres_medium,
+    plane_source,
     random_field,
     CONFIGS,
     config_problem,

@@ -19,6 +19,8 @@ __all__ = [
     "gaussian_random_field_medium",
     "point_source",
     "gaussian_beam_plane_source",
+    "packed_spheres_medium",
+    "plane_source",
     "random_field",
     "CONFIGS",
     "config_problem",
@@ -84,6 +86,79 @@ def fill_spheres_medium(shape, fill, r_range, n_range, seed, background=1.0, mar
         cv |= mask
         n[sl][mask] = v
     return n
+
+
+def packed_spheres_medium(shape, radius, clearance, value, seed, background=1.0, margin=(0, 0, 0),
+                          periodic=(False, False, False), max_failures=2000, dtype=np.complex64,
+                          return_centres=False):
+    """Spheres of one ``radius`` and index ``value`` placed by random sequential
+    addition: candidate centres are drawn uniformly in the box shrunk by
+    ``margin[d]`` pixels on both faces of axis d, and a candidate is kept when
+    its centre lies at least 2 radius + clearance from every kept centre
+    (distances wrap on the periodic axes). Placement stops after
+    ``max_failures`` rejections in a row. Spheres that cross a periodic face are
+    painted on both sides. The kind of structure the paper's large example uses
+    (Sec. 4.3: tightly packed spheres of radius 6 wavelengths with a clearance of
+    6 wavelengths, index 1.33 + 0.01i in a background of 1)."""
+    rng = np.random.default_rng(seed)
+    n = np.full(shape, background, dtype=dtype)
+    dmin = 2.0 * radius + clearance
+    cell = dmin
+    ncell = [max(1, int(s // cell)) for s in shape]
+    grid = {}
+    centres = []
+    lo = [float(m) for m in margin]
+    hi = [float(s - m) for s, m in zip(shape, margin)]
+    fails = 0
+    while fails < max_failures:
+        c = np.array([rng.uniform(l, max(l, h)) for l, h in zip(lo, hi)])
+        key = [min(int(c[d] // cell), ncell[d] - 1) for d in range(3)]
+        ok = True
+        for off in np.ndindex(3, 3, 3):
+            k = []
+            for d in range(3):
+                v = key[d] + off[d] - 1
+                if periodic[d]:
+                    v %= ncell[d]
+                elif v < 0 or v >= ncell[d]:
+                    break
+                k.append(v)
+            if len(k) < 3:
+                continue
+            for j in grid.get(tuple(k), ()):
+                dv = np.abs(centres[j] - c)
+                for d in range(3):
+                    if periodic[d]:
+                        dv[d] = min(dv[d], shape[d] - dv[d])
+                if float(dv @ dv) < dmin * dmin:
+                    ok = False
+                    break
+            if not ok:
+                break
+        if not ok:
+            fails += 1
+            continue
+        fails = 0
+        grid.setdefault(tuple(key), []).append(len(centres))
+        centres.append(c)
+    for c in centres:
+        shifts = [[0.0] + ([float(shape[d]), -float(shape[d])] if periodic[d] else []) for d in range(3)]
+        for s0 in shifts[0]:
+            for s1 in shifts[1]:
+                for s2 in shifts[2]:
+                    _paint_sphere(n, (c[0] + s0, c[1] + s1, c[2] + s2), radius, value)
+    if return_centres:
+        return n, np.array(centres).reshape(-1, 3)
+    return n
+
+
+def plane_source(shape, axis=0, index=0, dtype=np.complex64):
+    """Unit amplitude on the whole plane ``axis == index`` (a plane wave's source)."""
+    s = np.zeros(shape, dtype=dtype)
+    idx = [slice(None)] * 3
+    idx[axis] = index
+    s[tuple(idx)] = 1.0
+    return s
 
 
 def gaussian_random_field_medium(shape, mean, std, corr_len, seed, dtype=np.complex64):
@@ -162,6 +237,17 @@ CONFIGS = {
                periodic=(False, False, False), widths=8, t=8, tol=1e-4,
                medium=("fill", dict(fill=0.30, r_range=(5, 40), n_range=(1.0, 1.5), seed=105, margin=8)),
                source=("point", dict())),
+    # The geometry of the paper's large example (Sec. 4.3): 330 x 320 x 320
+    # wavelengths at 4 points per wavelength, absorbing layers of 5 wavelengths on
+    # the x faces only, y and z periodic, a plane source at x = 0 of the structure,
+    # packed spheres of radius 6 and clearance 6 wavelengths. On one GPU the y and
+    # z axes are split too (periodic seams), into 7-smooth subdomain edges.
+    "P43": dict(shape=(1320, 1280, 1280), pixel=0.25, wavelength=1.0, split=(5, 4, 4),
+                split_sizes=((280, 280, 256, 252, 252), (320,) * 4, (320,) * 4),
+                periodic=(False, True, True), widths=((20, 20), (0, 0), (0, 0)), t=8, tol=1e-6,
+                medium=("packed", dict(radius=24.0, clearance=24.0, value=1.33 + 0.01j, seed=107,
+                                       margin=(44, 0, 0), periodic=(False, True, True))),
+                source=("plane", dict(axis=0, index=20))),
 }
 
 
@@ -180,6 +266,8 @@ def config_problem(name, shape=None):
         n = spheres_medium(shp, **kw)
     elif kind == "fill":
         n = fill_spheres_medium(shp, **kw)
+    elif kind == "packed":
+        n = packed_spheres_medium(shp, **kw)
     elif kind == "grf":
         n = gaussian_random_field_medium(shp, **kw)
     else:
@@ -189,12 +277,17 @@ def config_problem(name, shape=None):
         src = point_source(shp, **skw)
     elif skind == "beam":
         src = gaussian_beam_plane_source(shp, **skw)
+    elif skind == "plane":
+        src = plane_source(shp, **skw)
     else:
         raise ValueError(skind)
     w = cfg["widths"]
+    widths = tuple(tuple(p) for p in w) if isinstance(w, tuple) else ((w, w), (w, w), (w, w))
     params = dict(shape=shp, pixel=cfg["pixel"], wavelength=cfg["wavelength"],
                   split=tuple(cfg["split"]), periodic=tuple(cfg["periodic"]),
-                  widths=((w, w), (w, w), (w, w)), t=cfg["t"], tol=cfg["tol"])
+                  widths=widths, t=cfg["t"], tol=cfg["tol"])
+    if cfg.get("split_sizes") is not None and shape is None:  # explicit sizes hold for the full grid only
+        params["split_sizes"] = [list(v) for v in cfg["split_sizes"]]
     return params, n, src
 
 

@@ -62,11 +62,17 @@ CASES = {
     "prime_sizes": dict(shape=(84, 47, 53), split=(2, 1, 1), t=4, split_sizes=[[41, 43], [47], [53]]),
     "prime_mixed": dict(shape=(40, 22, 59), split=(2, 2, 1), t=3, split_sizes=[[16, 24], [11, 11], [59]],
                         periodic=(False, False, True)),
+    # the boundary conditions of the paper's large example (Sec. 4.3): absorbing layers on the x
+    # faces only, y and z periodic and split across their seams, uneven x subdomains
+    "paper_geometry": dict(shape=(44, 32, 32), split=(2, 2, 2), t=4, periodic=(False, True, True),
+                           widths=((6, 6), (0, 0), (0, 0)), split_sizes=[[24, 20], [16, 16], [16, 16]]),
 }
 
 
-TF32_CASES = ["cube_2x2x2", "uneven_sizes", "single_nonperiodic", "periodic_split_seam", "t_sweep_6", "prime_sizes"]
-RES_CASES = ["cube_2x2x2", "single_periodic", "ragged_3x1x2", "line_1d", "t8_2x2x2", "t_sweep_16", "prime_sizes"]
+TF32_CASES = ["cube_2x2x2", "uneven_sizes", "single_nonperiodic", "periodic_split_seam", "t_sweep_6", "prime_sizes",
+              "paper_geometry"]
+RES_CASES = ["cube_2x2x2", "single_periodic", "ragged_3x1x2", "line_1d", "t8_2x2x2", "t_sweep_16", "prime_sizes",
+             "paper_geometry"]
 PLAIN_CASES = ["cube_2x2x2", "uneven_sizes", "periodic_split_seam", "t8_2x2x2", "prime_sizes", "single_periodic"]
 
 
