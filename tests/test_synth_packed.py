@@ -51,3 +51,23 @@ def test_plane_source_and_paper_geometry_recipe():
     assert params["widths"] == ((20, 20), (0, 0), (0, 0))
     assert "split_sizes" not in params  # explicit sizes belong to the full grid
     assert np.count_nonzero(src) == 64 * 64 and np.all(src[20] == 1)
+
+
+def test_paper_geometry_split_fits_the_library():
+    """The full-size P43 split: the sizes add up to the grid, every edge is a
+    mixed-radix length of at most 512 (2, 3, 5, 7 only) and at least 2t on every
+    corrected axis, and the absorbing layers sit on the x faces only."""
+    from synth import CONFIGS
+
+    cfg = CONFIGS["P43"]
+    shape, sizes, t = cfg["shape"], cfg["split_sizes"], cfg["t"]
+    assert [sum(s) for s in sizes] == list(shape)
+    assert [len(s) for s in sizes] == list(cfg["split"])
+    for s in sizes:
+        for n in s:
+            m = n
+            for q in (2, 3, 5, 7):
+                while m % q == 0:
+                    m //= q
+            assert m == 1 and 2 * t <= n <= 512, n
+    assert cfg["widths"] == ((20, 20), (0, 0), (0, 0)) and cfg["periodic"] == (False, True, True)
