@@ -84,3 +84,29 @@ def test_320_edge_tma_passes_equal_register_fed_passes(oracle_runs, geom):
         xs.append(x)
         plan.close()
     assert torch.equal(xs[0], xs[1])
+
+
+# Axis-2 edges above 256 other than 320, whose row tiles use the general
+# (row, element) enumeration of the first pass (343 = 7^3 with 21 warps per CTA,
+# 270 with 16): the first pass copies x into its tile with cp.async there.
+WIDE = {"343": (32, 32, 686), "270": (32, 32, 540)}
+
+
+@pytest.mark.parametrize("edge", sorted(WIDE))
+def test_wide_axis2_edge_iterations_match_oracle(edge):
+    import paper_2410_02395_gb300 as pkg
+
+    shape = WIDE[edge]
+    n = spheres_medium(shape, count=5, r_range=(3, 10), n_range=(1.0, 1.5), seed=343, margin=8)
+    src = point_source(shape)
+    ref = Problem(n, 0.25, 1.0, widths=KW["widths"], split=KW["split"], t=KW["t"])
+    assert int(edge) in ref.sizes[2]
+    x10r, _, histr = ref.solve(src, tol=0.0, max_iter=10)
+    plan = pkg.Plan(shape, 0.25, 1.0, torch.from_numpy(n).cuda(), boundary_widths=KW["widths"], split=KW["split"],
+                    truncation=KW["t"], graph_iters=5)
+    x10, it10, _, hist = plan.solve(torch.from_numpy(src).cuda(), tol=0.0, max_iter=10, with_history=True)
+    assert it10 == 10
+    err = relative_l2(x10.cpu().numpy(), x10r)
+    assert err < ITER_TOL, err
+    np.testing.assert_allclose(hist, np.array(histr), rtol=1e-4, atol=1e-6)
+    plan.close()
